@@ -1,0 +1,525 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test checks the oracle against something other than itself: closed
+forms (affine maps, quadratic fields, the trapezoid rule), algebraic
+identities the paper states or that follow from it, a brute-force restatement
+of the loop integral on tiny grids, second-order convergence to analytic
+currents, the Cash-Karp order conditions, and the physics of magneto-friction
+(energy decay, symmetry, stationary states).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import glemur_inputs as gi
+import oracle as ora
+
+
+def rand_grid(n, seed, amp=0.03, lo=-1.0, hi=1.0):
+    """Smooth random distortion of a uniform grid (all nodes moved)."""
+    g = gi.Grid(n, n, n, (lo,) * 3, (hi,) * 3)
+    X = gi.nodes(g)
+    rng = np.random.default_rng(seed)
+    x = X.copy()
+    for a in range(3):
+        for _ in range(3):
+            kv = rng.integers(1, 3, size=3)
+            ph = rng.uniform(0, 2 * np.pi, size=3)
+            amp_a = amp * rng.uniform(0.3, 1.0)
+            x[a] += amp_a * np.sin(kv[0] * X[0] + ph[0]) * np.sin(kv[1] * X[1] + ph[1]) * \
+                np.sin(kv[2] * X[2] + ph[2])
+    return g, X, x
+
+
+def interior(v):
+    return v[:, 1:-1, 1:-1, 1:-1]
+
+
+# --------------------------------------------------------------- affine maps
+
+
+def affine_case(seed, n=7):
+    rng = np.random.default_rng(seed)
+    g = gi.Grid(n, n + 1, n + 2, (-1.0, -0.5, -2.0), (1.0, 1.5, 0.5))
+    X = gi.nodes(g)
+    A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+    while np.linalg.det(A) < 0.3:
+        A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+    t = rng.standard_normal(3)
+    b = rng.standard_normal(3)
+    G = rng.standard_normal((3, 3))
+    G -= np.trace(G) / 3 * np.eye(3)             # div B0 = tr G = 0
+    x = np.einsum("ab,b...->a...", A, X) + t[:, None, None, None]
+    B0 = b[:, None, None, None] + np.einsum("ab,b...->a...", G, X)
+    return g, X, x, B0, A, G, b
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pullback_exact_on_affine_map(seed):
+    g, X, x, B0, A, G, b = affine_case(seed)
+    B, D, rc = ora.pullback(g, x, B0)
+    assert rc == ora.OK
+    detA = np.linalg.det(A)
+    expect = np.einsum("ab,b...->a...", A, B0) / detA
+    assert np.allclose(D, detA, rtol=1e-13, atol=0)
+    assert np.abs(B - expect).max() <= 1e-12 * np.abs(expect).max()
+
+
+@pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_current_exact_on_affine_map(seed, curl):
+    """x = A X + t, B0 = b + G X (tr G = 0): B(x) = A (b + G A^-1 (x - t)) /
+    det A is affine in x, so curl_x B = eps : (A G A^-1 / det A) everywhere
+    and both discrete currents must reproduce it to rounding."""
+    g, X, x, B0, A, G, b = affine_case(seed)
+    L = A @ G @ np.linalg.inv(A) / np.linalg.det(A)    # L[m, l] = dB_m / dx_l
+    Jex = np.array([L[2, 1] - L[1, 2], L[0, 2] - L[2, 0], L[1, 0] - L[0, 1]])
+    if curl == ora.MIMETIC:
+        B, _, _ = ora.pullback(g, x, B0)
+        J, gap, rc = ora.curl_mimetic(g, x, B)
+        assert gap < 1e-13
+    else:
+        J, rc = ora.curl_direct(g, x, B0)
+    assert rc == ora.OK
+    err = np.abs(interior(J) - Jex[:, None, None, None]).max()
+    assert err <= 1e-11 * max(np.abs(Jex).max(), np.abs(L).max())
+    # the current is only defined inside; the boundary is line-tied
+    Jb = J.copy()
+    Jb[:, 1:-1, 1:-1, 1:-1] = 0
+    assert np.all(Jb == 0)
+
+
+def test_flux_through_closed_cells_vanishes_on_affine_map():
+    """B = F B0 / Delta is the push-forward of a solenoidal field: the net
+    flux out of every deformed (parallelepiped) cell is zero to rounding, and
+    the flux through each deformed face equals that of B0 through the
+    undeformed face (Nanson).  A transposed F, or a missing 1/Delta, breaks
+    both."""
+    g, X, x, B0, A, G, b = affine_case(7, n=6)
+    B, _, _ = ora.pullback(g, x, B0)
+
+    def face_flux(pos, fld, sl_a, sl_b, sl_c, sl_d):
+        # face with corners a, b, c, d in cyclic order: vector area by the
+        # diagonals, field by the corner mean (exact for affine fields)
+        d1 = pos[sl_c] - pos[sl_a]
+        d2 = pos[sl_d] - pos[sl_b]
+        nA = 0.5 * np.cross(d1, d2, axis=0)
+        Bm = 0.25 * (fld[sl_a] + fld[sl_b] + fld[sl_c] + fld[sl_d])
+        return (Bm * nA).sum(axis=0)
+
+    def S(i, j, k):
+        return (slice(None), slice(k, k + g.nz - 1), slice(j, j + g.ny - 1),
+                slice(i, i + g.nx - 1))
+
+    def net(pos, fld):
+        # outward flux through the 6 faces of every cell (i..i+1, j.., k..)
+        fx1 = face_flux(pos, fld, S(1, 0, 0), S(1, 1, 0), S(1, 1, 1), S(1, 0, 1))
+        fx0 = face_flux(pos, fld, S(0, 0, 0), S(0, 1, 0), S(0, 1, 1), S(0, 0, 1))
+        fy1 = face_flux(pos, fld, S(0, 1, 0), S(0, 1, 1), S(1, 1, 1), S(1, 1, 0))
+        fy0 = face_flux(pos, fld, S(0, 0, 0), S(0, 0, 1), S(1, 0, 1), S(1, 0, 0))
+        fz1 = face_flux(pos, fld, S(0, 0, 1), S(1, 0, 1), S(1, 1, 1), S(0, 1, 1))
+        fz0 = face_flux(pos, fld, S(0, 0, 0), S(1, 0, 0), S(1, 1, 0), S(0, 1, 0))
+        return fx1 - fx0 + fy1 - fy0 + fz1 - fz0, fx1
+
+    net_x, face_x = net(x, B)
+    net_X, face_X = net(X, B0)
+    scale = np.abs(face_x).max()
+    assert np.abs(net_x).max() <= 1e-12 * scale
+    assert np.abs(net_X).max() <= 1e-12 * scale
+    assert np.abs(face_x - face_X).max() <= 1e-12 * scale
+
+
+# --------------------------------------------------------- undistorted grids
+
+
+@pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
+def test_current_exact_for_quadratic_field_on_uniform_grid(curl):
+    """x = X and the solenoidal quadratic B0 = (y^2, z^2, x^2): central
+    differences are exact for quadratics, so J = curl B0 = (-2z, -2x, -2y)."""
+    g = gi.Grid(9, 8, 10)
+    X = gi.nodes(g)
+    B0 = np.stack([X[1] ** 2, X[2] ** 2, X[0] ** 2])
+    if curl == ora.MIMETIC:
+        B, _, _ = ora.pullback(g, X, B0)
+        assert np.abs(B - B0).max() < 1e-14
+        J, _, rc = ora.curl_mimetic(g, X, B)
+    else:
+        J, rc = ora.curl_direct(g, X, B0)
+    assert rc == ora.OK
+    Jex = np.stack([-2 * X[2], -2 * X[0], -2 * X[1]])
+    assert np.abs(interior(J) - interior(Jex)).max() < 1e-12
+
+
+def test_mimetic_reduces_to_central_difference_curl_on_uniform_grid():
+    """On x = X the nearest-neighbour loops give exactly the second-order
+    central-difference curl (textbook routine: numpy.gradient)."""
+    g = gi.Grid(11, 12, 13, (-1.0, -1.2, -0.7), (1.3, 1.0, 1.1))
+    X = gi.nodes(g)
+    B0 = gi.braid_field(X, gi.braid_regions(3, None, True, l=0.5, L=0.5))
+    B, _, _ = ora.pullback(g, X, B0)
+    J, _, rc = ora.curl_mimetic(g, X, B)
+    h = g.h
+    d = [[np.gradient(B0[m], h[2 - n], axis=n) for n in range(3)] for m in range(3)]
+    # array axes (0, 1, 2) = (z, y, x): dB_m/dx = d[m][2], /dy = d[m][1], /dz = d[m][0]
+    Jcd = np.stack([d[2][1] - d[1][0], d[0][0] - d[2][2], d[1][2] - d[0][1]])
+    assert rc == ora.OK
+    assert np.abs(interior(J) - interior(Jcd)).max() < 1e-12 * np.abs(Jcd).max()
+
+
+# ----------------------------------------------------- algebraic identities
+
+
+def test_four_surfaces_equals_sum_of_triangles():
+    """Eq. "four surfaces" and eq. "sum of triangles" give the same vector
+    area on arbitrarily distorted loops (the apex x_ijk drops out)."""
+    g, X, x = rand_grid(8, 11, amp=0.15)
+    B0 = gi.uniform_field(g)
+    B, _, _ = ora.pullback(g, x, B0)
+    J, gap, rc = ora.curl_mimetic(g, x, B)
+    assert gap < 1e-13
+
+
+def test_mimetic_equals_curl_of_nodal_gradient():
+    """Derived identity: with g_a = x(+e_a) - x(-e_a) and
+    P_a = B(+e_a) - B(-e_a) at an interior node, the three loop equations
+    J . (g_p x g_q) = P_p . g_q - P_q . g_p (cyclic p, q) are solved by the
+    curl of dB/dx = P G^-1.  Checked on a distorted grid with a twisted
+    field, node by node through numpy.linalg."""
+    g, X, x = rand_grid(9, 5, amp=0.05)
+    B0 = gi.braid_field(X, gi.braid_regions(2, None, True, l=0.6, L=0.6))
+    B, _, _ = ora.pullback(g, x, B0)
+    J, _, rc = ora.curl_mimetic(g, x, B)
+    assert rc == ora.OK
+    worst = 0.0
+    for k in range(1, g.nz - 1):
+        for j in range(1, g.ny - 1):
+            for i in range(1, g.nx - 1):
+                c = np.array([k, j, i])
+                Gm = np.zeros((3, 3))
+                P = np.zeros((3, 3))
+                for a in range(3):
+                    e = np.zeros(3, int)
+                    e[2 - a] = 1
+                    p, m = tuple(c + e), tuple(c - e)
+                    Gm[:, a] = x[(slice(None),) + p] - x[(slice(None),) + m]
+                    P[:, a] = B[(slice(None),) + p] - B[(slice(None),) + m]
+                L = P @ np.linalg.inv(Gm)
+                Jn = np.array([L[2, 1] - L[1, 2], L[0, 2] - L[2, 0], L[1, 0] - L[0, 1]])
+                worst = max(worst, np.abs(Jn - J[:, k, j, i]).max())
+    assert worst < 1e-11 * np.abs(J).max()
+
+
+def test_loop_integral_brute_force_tiny_grid():
+    """Brute force on a 4^3 grid: circulation by 3-point Gauss-Legendre
+    quadrature of the linearly interpolated B along each straight loop edge,
+    vector area by Newell's polygon formula, numpy.linalg.solve for J."""
+    g, X, x = rand_grid(4, 3, amp=0.08)
+    B0 = gi.braid_field(X, gi.braid_regions(2, None, True, l=0.7, L=0.7))
+    B, _, _ = ora.pullback(g, x, B0)
+    J, _, rc = ora.curl_mimetic(g, x, B)
+    gl_t = np.array([-math.sqrt(3 / 5), 0.0, math.sqrt(3 / 5)])
+    gl_w = np.array([5 / 9, 8 / 9, 5 / 9])
+    for k in (1, 2):
+        for j in (1, 2):
+            for i in (1, 2):
+                M = np.zeros((3, 3))
+                circ = np.zeros(3)
+                for r in range(3):
+                    p, q = (r + 1) % 3, (r + 2) % 3
+                    offs = []
+                    for (ax, sgn) in ((p, 1), (q, 1), (p, -1), (q, -1)):
+                        o = [i, j, k]
+                        o[ax] += sgn
+                        offs.append(o)
+                    P = [x[:, o[2], o[1], o[0]] for o in offs]
+                    Bv = [B[:, o[2], o[1], o[0]] for o in offs]
+                    s = 0.0
+                    for m in range(4):
+                        a0, a1 = P[m], P[(m + 1) % 4]
+                        b0, b1 = Bv[m], Bv[(m + 1) % 4]
+                        for t, w in zip(gl_t, gl_w):
+                            lam = 0.5 * (t + 1)
+                            s += 0.5 * w * np.dot((1 - lam) * b0 + lam * b1, a1 - a0)
+                    circ[r] = s
+                    nA = np.zeros(3)
+                    for m in range(4):
+                        nA += 0.5 * np.cross(P[m], P[(m + 1) % 4])
+                    M[r] = nA
+                Jb = np.linalg.solve(M, circ)
+                assert np.abs(Jb - J[:, k, j, i]).max() < 1e-12 * max(1.0, np.abs(Jb).max())
+
+
+# ------------------------------------------------- convergence on a smooth map
+
+
+def _analytic_case():
+    import sympy as sp
+    Xs, Ys, Zs = sp.symbols("X Y Z", real=True)
+    eps = sp.Rational(1, 20)
+    xs = [Xs + eps * sp.sin(2 * Ys + 1) * sp.cos(Zs),
+          Ys + eps * sp.sin(2 * Zs) * sp.cos(Xs + sp.Rational(1, 2)),
+          Zs + eps * sp.sin(Xs + Ys)]
+    G = sp.exp(-(Xs ** 2 + Ys ** 2) / sp.Rational(1, 2) - Zs ** 2)
+    B0 = [-Ys * G, Xs * G, sp.Integer(1)]
+    Xv = [Xs, Ys, Zs]
+    F = sp.Matrix(3, 3, lambda a, b: sp.diff(xs[a], Xv[b]))
+    D = F.det()
+    Bv = (F * sp.Matrix(B0)) / D
+    dB = sp.Matrix(3, 3, lambda m, n: sp.diff(Bv[m], Xv[n]))
+    gB = dB * F.inv()                                # gB[m, l] = dB_m / dx_l
+    Jv = [gB[2, 1] - gB[1, 2], gB[0, 2] - gB[2, 0], gB[1, 0] - gB[0, 1]]
+    f = sp.lambdify((Xs, Ys, Zs), [xs, B0, list(Bv), Jv], "numpy")
+    return f
+
+
+@pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
+def test_second_order_convergence_on_nonlinear_map(curl):
+    """On a smooth nonlinear map with a twisted B0, B and J converge to the
+    analytic B = F B0/Delta and curl_x B at second order (errors drop ~4x per
+    halving of h).  Exercises the second-derivative terms of the direct
+    current and the one-sided boundary Jacobian."""
+    f = _analytic_case()
+    errs_J, errs_B = [], []
+    for n in (9, 17, 33):
+        g = gi.Grid(n, n, n)
+        X = gi.nodes(g)
+        xs, B0, Bex, Jex = f(X[0], X[1], X[2])
+        bc = lambda v: np.stack([np.broadcast_to(np.asarray(c, float), X[0].shape) for c in v])
+        x, B0, Bex, Jex = bc(xs), bc(B0), bc(Bex), bc(Jex)
+        B, _, rc = ora.pullback(g, x, B0)
+        assert rc == ora.OK
+        if curl == ora.MIMETIC:
+            J, _, rc = ora.curl_mimetic(g, x, B)
+        else:
+            J, rc = ora.curl_direct(g, x, B0)
+        assert rc == ora.OK
+        errs_B.append(np.abs(B - Bex).max())
+        errs_J.append(np.abs(interior(J) - interior(Jex)).max())
+    for e in (errs_B, errs_J):
+        assert e[0] / e[1] > 3.3 and e[1] / e[2] > 3.6, e
+    assert errs_J[-1] < 2e-2 * np.abs(Jex).max()
+
+
+# --------------------------------------------------------------- energy
+
+
+def test_energy_of_uniform_field_is_exact():
+    """zeta weights make eq. "magnetic energy" the trapezoid rule: for
+    x = A X and uniform B0, B = A B0 / det A and E = |A B0|^2/(2 det A) V."""
+    g = gi.Grid(6, 7, 9)
+    X = gi.nodes(g)
+    B0 = gi.uniform_field(g)
+    E, rc = ora.energy(g, X, B0)
+    assert rc == ora.OK and abs(E - 4.0) < 1e-13
+    A = np.array([[1.1, 0.2, 0.0], [-0.1, 0.9, 0.3], [0.05, 0.0, 1.2]])
+    b = np.array([0.3, -0.5, 1.0])
+    x = np.einsum("ab,b...->a...", A, X)
+    B0 = np.broadcast_to(b[:, None, None, None], X.shape).copy()
+    E, rc = ora.energy(g, x, B0)
+    Ab = A @ b
+    assert abs(E - 0.5 * Ab @ Ab / np.linalg.det(A) * 8.0) < 1e-12
+
+
+def test_energy_converges_to_integral():
+    """On x = X the energy of a smooth field converges at second order to
+    the integral of B^2/2 (computed by scipy's adaptive cubature)."""
+    from scipy import integrate
+    reg = (0.0, 0.0, 0.0, 1.0, 0.5, 1.0)
+
+    def dens(z, y, x):
+        G = math.exp(-(x * x + y * y) / 0.25 - z * z)
+        return 0.5 * ((y * G) ** 2 + (x * G) ** 2 + 1.0)
+
+    exact, _ = integrate.tplquad(dens, -1, 1, -1, 1, -1, 1, epsabs=1e-12, epsrel=1e-12)
+    errs = []
+    for n in (9, 17, 33):
+        g = gi.Grid(n, n, n)
+        X = gi.nodes(g)
+        E, _ = ora.energy(g, X, gi.braid_field(X, [reg]))
+        errs.append(abs(E - exact))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.8, errs
+
+
+def test_energy_rate_matches_lorentz_power():
+    """Magneto-friction: along u = J x B the energy changes at
+    dE/dt = -int |J x B|^2 dV (no boundary term: the twist is localised well
+    inside the line-tied box).  A central difference of the oracle's E along
+    its own u agrees with -sum zeta |u|^2 Delta h^3 at second order in h; a
+    sign or factor error in u, J or B fails this."""
+    rel = []
+    for n in (17, 33):
+        g = gi.Grid(n, n, n)
+        X = gi.nodes(g)
+        B0 = gi.braid_field(X, [(0.0, 0.0, 0.0, 1.0, 0.3, 0.3)])
+        x = X
+        u, rc = ora.velocity(g, x, B0)
+        eps = 1e-5
+        Ep, _ = ora.energy(g, x + eps * u, B0)
+        Em, _ = ora.energy(g, x - eps * u, B0)
+        dEdt = (Ep - Em) / (2 * eps)
+        _, D, _ = ora.pullback(g, x, B0)
+        power = -((u ** 2).sum(0) * D).sum() * np.prod(g.h)    # u = 0 on the boundary
+        assert dEdt < 0
+        rel.append(abs(dEdt - power) / abs(power))
+    assert rel[0] < 0.05 and rel[0] / rel[1] > 3.0, rel
+
+
+# ------------------------------------------------------------ Cash-Karp
+
+
+def test_cash_karp_order_conditions():
+    c, a, b5, b4 = ora.cash_karp_tableau()
+    assert np.allclose(a.sum(1), c, atol=1e-15)
+    # order conditions up to 5 for b5 and up to 4 for b4
+    conds = [
+        (lambda b: b.sum(), 1.0),
+        (lambda b: b @ c, 1 / 2),
+        (lambda b: b @ c ** 2, 1 / 3),
+        (lambda b: b @ (a @ c), 1 / 6),
+        (lambda b: b @ c ** 3, 1 / 4),
+        (lambda b: b @ (c * (a @ c)), 1 / 8),
+        (lambda b: b @ (a @ c ** 2), 1 / 12),
+        (lambda b: b @ (a @ (a @ c)), 1 / 24),
+    ]
+    conds5 = [
+        (lambda b: b @ c ** 4, 1 / 5),
+        (lambda b: b @ (c ** 2 * (a @ c)), 1 / 10),
+        (lambda b: b @ ((a @ c) ** 2), 1 / 20),
+        (lambda b: b @ (c * (a @ c ** 2)), 1 / 15),
+        (lambda b: b @ (a @ c ** 3), 1 / 20),
+        (lambda b: b @ (c * (a @ (a @ c))), 1 / 30),
+        (lambda b: b @ (a @ (c * (a @ c))), 1 / 40),
+        (lambda b: b @ (a @ (a @ c ** 2)), 1 / 60),
+        (lambda b: b @ (a @ (a @ (a @ c))), 1 / 120),
+    ]
+    for fn, v in conds:
+        assert abs(fn(b5) - v) < 1e-14 and abs(fn(b4) - v) < 1e-14
+    for fn, v in conds5:
+        assert abs(fn(b5) - v) < 1e-14
+    # the embedded pair really differs at fifth order
+    assert max(abs(fn(b4) - v) for fn, v in conds5) > 1e-4
+
+
+def test_cash_karp_convergence_scalar_ode():
+    """y' = -y: one-step error of the 5th-order solution ~ dt^6, the embedded
+    estimate ~ dt^5."""
+    errs, ests = [], []
+    for dt in (0.2, 0.1, 0.05):
+        yn, ye, _, rc = ora.ck_attempt(np.array([1.0]), dt, lambda y: -y)
+        assert rc == ora.OK
+        errs.append(abs(yn[0] - math.exp(-dt)))
+        ests.append(abs(ye[0]))
+    for e, p in ((errs, 6), (ests, 5)):
+        r1, r2 = e[0] / e[1], e[1] / e[2]
+        assert 2 ** p * 0.8 < r1 < 2 ** p * 1.25 and 2 ** p * 0.85 < r2 < 2 ** p * 1.15, e
+
+
+def test_cash_karp_exact_for_quartic_in_time():
+    """Quadrature case y' = f(t) (t carried as a state with t' = 1): a
+    fifth-order method integrates a quartic in t exactly."""
+    def rhs(y):
+        t = y[1]
+        return np.array([1 + t - 2 * t ** 2 + 3 * t ** 3 + 5 * t ** 4, 1.0])
+    dt = 0.37
+    yn, ye, _, rc = ora.ck_attempt(np.array([0.0, 0.0]), dt, rhs)
+    exact = dt + dt ** 2 / 2 - 2 * dt ** 3 / 3 + 3 * dt ** 4 / 4 + dt ** 5
+    assert abs(yn[0] - exact) < 1e-15 and abs(yn[1] - dt) < 1e-16
+
+
+# ---------------------------------------------------------- step control
+
+
+def test_step_control_rules():
+    o = ora.ControlOpts(lambda0=1e-6)
+    rc, dtn, acc = ora.step_control(o, 2e-6, 1e-3)             # reject, shrink
+    assert rc == ora.OK and acc == 0
+    assert abs(dtn - 1e-3 * 0.5 ** 0.2) < 1e-18
+    rc, dtn, acc = ora.step_control(o, 0.7e-6, 1e-3)           # keep
+    assert acc == 1 and dtn == 1e-3
+    rc, dtn, acc = ora.step_control(o, 1e-6, 1e-3)             # boundary: accept
+    assert acc == 1 and dtn == 1e-3
+    rc, dtn, acc = ora.step_control(o, 0.25e-6, 1e-3)          # grow
+    assert acc == 1 and abs(dtn - 1e-3 * 4 ** 0.2) < 1e-18
+    rc, dtn, acc = ora.step_control(o, 0.0, 1e-3)              # clamp (5x)
+    assert acc == 1 and abs(dtn - 5e-3) < 1e-18
+    rc, dtn, acc = ora.step_control(o, 1e3, 1e-3)              # clamp (0.1x)
+    assert acc == 0 and abs(dtn - 1e-4) < 1e-19
+    rc, dtn, acc = ora.step_control(o, float("nan"), 1e-3)
+    assert rc == ora.ERR_NONFINITE
+    rc, dtn, acc = ora.step_control(o, 1e-5, 1e-3, consecutive_rejects=64)
+    assert rc == ora.ERR_DT_UNDERFLOW
+    rc, dtn, acc = ora.step_control(ora.ControlOpts(lambda0=1e-6, dt_min=1e-3), 1e-5, 1e-3)
+    assert rc == ora.ERR_DT_UNDERFLOW
+
+
+# --------------------------------------------------------------- physics
+
+
+def test_uniform_field_is_stationary_on_affine_grid():
+    g, X, x, B0, A, G, b = affine_case(4, n=6)
+    B0 = np.broadcast_to(b[:, None, None, None], X.shape).copy()
+    u, rc = ora.velocity(g, x, B0)
+    assert np.abs(u).max() < 1e-12
+    xn, dt, log, st, rc = ora.relax(g, x, B0, 3, 1e-3)
+    assert rc == ora.OK and st["rejected"] == 0
+    assert np.abs(xn - x).max() < 1e-13
+    assert abs(dt - 1e-3 * 5 ** 3) < 1e-15          # grows at the clamp
+
+
+def test_energy_decays_monotonically():
+    w = gi.make_workload("tube", n=12)
+    x = w.x0
+    dt = 1e-3
+    E0, _ = ora.energy(w.grid, x, w.B0)
+    Es = [E0]
+    for _ in range(8):
+        x, dt, log, st, rc = ora.relax(w.grid, x, w.B0, 5, dt,
+                                       opts=ora.ControlOpts(lambda0=1e-7))
+        assert rc == ora.OK
+        Es.append(ora.energy(w.grid, x, w.B0)[0])
+    d = np.diff(Es)
+    assert np.all(d <= 1e-13 * E0), d
+    assert Es[-1] < Es[0] - 1e-6
+
+
+def test_rotation_equivariance_of_a_step():
+    """The tube on a symmetric grid is invariant under the quarter turn
+    (x, y) -> (-y, x); so is one relaxation step of the oracle."""
+    w = gi.make_workload("tube", n=10)
+    g = w.grid
+    xn, lam, rc = ora.step_fixed(g, w.x0, w.B0, 2e-3)
+    assert rc == ora.OK
+
+    def rot(v):
+        # value at node (i', j') = (n-1-j, i) is R v(i, j), R (a, b) = (-b, a)
+        Rv = np.stack([-v[1], v[0], v[2]])
+        out = np.empty_like(v)
+        n = g.nx
+        for j in range(g.ny):
+            for i in range(g.nx):
+                out[:, :, i, n - 1 - j] = Rv[:, :, j, i]
+        return out
+
+    assert np.abs(rot(w.x0) - w.x0).max() < 1e-15
+    assert np.abs(rot(w.B0) - w.B0).max() < 1e-15
+    assert np.abs(rot(xn) - xn).max() < 1e-14
+    assert np.abs(xn - w.x0).max() > 1e-5
+
+
+def test_collapsed_grid_is_reported():
+    g = gi.Grid(5, 5, 5)
+    X = gi.nodes(g)
+    x = X.copy()
+    x[0, 2, 2, 2] = X[0, 2, 2, 4] + 0.3      # fold node (2,2,2) past node (4,2,2)
+    _, _, rc = ora.pullback(g, x, gi.uniform_field(g))
+    assert rc == ora.ERR_COLLAPSED
+
+
+def test_velocity_at_matches_field():
+    w = gi.make_workload("braid", n=12)
+    for curl in (ora.MIMETIC, ora.DIRECT):
+        u, rc = ora.velocity(w.grid, w.x0, w.B0, curl)
+        for (i, j, k) in [(1, 1, 1), (5, 7, 3), (10, 10, 10), (0, 4, 4)]:
+            un, rc = ora.velocity_at(w.grid, w.x0, w.B0, i, j, k, curl)
+            assert np.array_equal(un, u[:, k, j, i])
