@@ -1,0 +1,335 @@
+"""Throughput of the Lagrangian magneto-frictional relaxation step on GB300.
+
+A step is one Cash-Karp attempt of the whole hot path (six fused stage
+kernels -- stage input, Jacobian, pull-back, current, J x B -- the
+fifth-order update with its embedded error, and the step control) over the
+64^3 braid workload (6 twist regions, pre-distorted grid, FP64, mimetic
+current).  Metric: interior node-stage updates per second (6 per interior
+node per attempt).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): every rank relaxes its own copy of the
+workload (replicas; the step has no cross-GPU exchange in this build) and
+`value` is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import glemur_inputs as gi  # noqa: E402
+
+METRIC = "node-stage updates/s"
+UNIT = "node-stage/s"
+# bytes moved per interior node-stage by the fused layout (stage s reads x,
+# B0 and k_1..k_{s-1}, writes k_s; the last writes x_new): 33 fields x 3
+# components per accepted step / 6 stages
+ALGO_BYTES = {"fp64": 132.0, "mixed": 66.0}
+# FP64 flops per interior node-stage of the mimetic stage kernel (FMA = 2),
+# counted once per node (halo recomputation excluded)
+ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0}
+FP64_PEAK_FLOPS = 1.25e12      # nominal dense FP64 rate of GB300 (152 SMs)
+L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes per stage launch from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum); None until a capture of the current kernels exists
+NCU_TRAFFIC = {}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name, n=None):
+    base, nn, _ = gi.WORKLOADS[name]
+    return gi.make_workload(base, n=n or nn)
+
+
+def config_dict(args, w):
+    g = w.grid
+    return {"workload": args.workload, "grid": [g.nx, g.ny, g.nz],
+            "interior_nodes": g.n_interior, "precision": args.precision, "curl": args.curl,
+            "fields": "braid of twist regions on a seeded pre-distorted grid" if
+            args.workload.startswith("braid") else args.workload,
+            "step": "one Cash-Karp attempt (6 stages + update/error + control)",
+            "l2": "flushed between timed steps (512 MiB write)",
+            "lambda0": 1e-7}
+
+
+# ------------------------------------------------------------------ oracle
+
+
+def run_oracle_sample(w, max_seconds, max_steps, curl):
+    """The FP64 CPU oracle as it stands, one Cash-Karp attempt per step on
+    the same workload, bounded in wall time."""
+    import oracle as ora
+    g = w.grid
+    x = w.x0.copy()
+    c = ora.MIMETIC if curl == "mimetic" else ora.DIRECT
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        x, lam, rc = ora.step_fixed(g, x, w.B0, 1e-4, c)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": g.n_interior * 6 * steps / dt, "unit": UNIT, "cores": 1,
+            "kind": "oracle", "seconds": dt, "steps": steps,
+            "sample": f"{steps} full FP64 Cash-Karp attempts of the oracle on the "
+                      f"{g.nx}x{g.ny}x{g.nz} workload, single thread"}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    for _ in range(min(args.warmup, 1)):
+        run_oracle_sample(w, 1e9, 1, args.curl)
+    cb = run_oracle_sample(w, 120.0, args.steps, args.curl)
+    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+           "steps": cb["steps"], "warmup": args.warmup,
+           "ms_per_step": 1e3 * cb["seconds"] / cb["steps"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference", "config": config_dict(args, w), "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+
+def time_mode(G, torch, w, precision, curl, steps, warmup, flush):
+    """Per-attempt, per-kernel CUDA-event times (ms) of `steps` attempts."""
+    r = G.Relaxation(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.lo, w.grid.hi,
+                     precision=G.MIXED if precision == "mixed" else G.FP64,
+                     curl=G.DIRECT if curl == "direct" else G.MIMETIC)
+    r.set_x(torch.from_numpy(w.x0).cuda())
+    r.set_B0(torch.from_numpy(w.B0).cuda())
+    for _ in range(warmup):
+        flush.zero_()
+        r.profile_attempt()
+    times = []
+    for _ in range(steps):
+        flush.zero_()                 # L2 flush, outside the event interval
+        times.append(r.profile_attempt())
+    st = r.stats()
+    return r, np.array(times), st
+
+
+def roofline_entry(ms, w, precision, curl, hbm_peak, peak_kind):
+    stage_ms = ms[:, :6].sum(axis=1).mean()            # the six stage launches
+    I = w.grid.n_interior
+    bytes_per_attempt = ALGO_BYTES[precision] * I * 6
+    gbs = bytes_per_attempt / (stage_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get((w.grid.nx, precision, curl))
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+           "frac": gbs / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+           "algorithmic_bytes_per_launch": bytes_per_attempt / 6}
+    if precision == "fp64":
+        fl = ALGO_FLOPS_F64[curl] * I * 6 / (stage_ms * 1e-3) / 1e12
+        alu = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_FLOPS / 1e12,
+               "unit": "TFLOP/s", "frac": fl * 1e12 / FP64_PEAK_FLOPS, "traffic": traffic,
+               "peak_kind": "nominal FP64 rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+               "algorithmic_flops_per_launch": ALGO_FLOPS_F64[curl] * I,
+               "hbm_frac": hbm["frac"], "hbm_achieved_gbs": gbs}
+        return alu
+    return hbm
+
+
+def e2e_measure(G, torch, w, precision, curl, steps):
+    """Same step through the C ABI with host buffers: H2D of x and B0 from
+    pinned memory, the attempt, D2H of the new positions, per step."""
+    r = G.Relaxation(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.lo, w.grid.hi,
+                     precision=G.MIXED if precision == "mixed" else G.FP64,
+                     curl=G.DIRECT if curl == "direct" else G.MIMETIC)
+    xh = torch.from_numpy(w.x0).pin_memory()
+    bh = torch.from_numpy(w.B0).pin_memory()
+    out = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        r.set_x(xh)
+        r.set_B0(bh)
+        r.attempts(1)
+        r.get_x(out=out.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r.set_x(xh)
+        r.set_B0(bh)
+        r.attempts(1)
+        r.get_x(out=out.numpy())
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    nbytes = w.x0.nbytes
+    return {"value": w.grid.n_interior * 6 / dt, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": dt * 1e3}
+
+
+def our_arm(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import paper_1405_0942_gb300 as G
+    G.lib()
+    hbm_peak, peak_kind = load_peaks()
+    w = workload(args.workload)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    sampler.start()
+    r, ms, st = time_mode(G, torch, w, args.precision, args.curl, args.steps, args.warmup, flush)
+    barrier()
+    clocks = sampler.stop()
+    total_s = ms.sum() * 1e-3                       # device time of the K timed steps
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    units = w.grid.n_interior * 6 * args.steps * ws
+    value = units / total_s
+    roof = roofline_entry(ms, w, args.precision, args.curl, hbm_peak, peak_kind)
+    per_kernel = ms.mean(axis=0).tolist()
+
+    extra = {}
+    if rank == 0 and ws == 1 and not args.no_compare:
+        for prec, curl in (("mixed", "mimetic"), ("fp64", "direct"), ("mixed", "direct")):
+            if (prec, curl) == (args.precision, args.curl):
+                continue
+            _, ms2, st2 = time_mode(G, torch, w, prec, curl, args.steps, args.warmup, flush)
+            v2 = w.grid.n_interior * 6 * args.steps / (ms2.sum() * 1e-3)
+            extra[f"{prec}_{curl}"] = {
+                "value": v2, "unit": UNIT, "ms_per_step": ms2.sum(axis=1).mean(),
+                "speedup_vs_primary": v2 / value,
+                "roofline": roofline_entry(ms2, w, prec, curl, hbm_peak, peak_kind)}
+    e2e = e2e_measure(G, torch, w, args.precision, args.curl, max(3, min(args.steps, 10)))
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return
+    cb = run_oracle_sample(w, 12.0, 1000, args.curl) if ws == 1 else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms.sum(axis=1).mean(),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded braid field and pre-distorted grid)",
+        "config": config_dict(args, w), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+        "clocks": clocks, "gpu_launches": r.kernels_per_attempt() * args.steps,
+        "kernel_ms": {"stages": per_kernel[:6], "control": per_kernel[6]},
+        "attempts": {"accepted": st["accepted"], "rejected": st["rejected"]},
+        "compare": extra,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="braid64", choices=sorted(gi.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--curl", default="mimetic", choices=["mimetic", "direct"])
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * glemur.h -- C ABI of the GB300 (sm_103a) library for Lagrangian
+ * magneto-frictional relaxation with the mimetic current (Candelaresi,
+ * Pontin & Hornig, "Mimetic Methods for Lagrangian Relaxation of Magnetic
+ * Fields", SIAM J. Sci. Comput.).
+ *
+ * The state is the position x(X, t) of every node of a logically
+ * rectangular grid of labels X_ijk = lo + (i h_x, j h_y, k h_z),
+ * h_a = (hi_a - lo_a) / (n_a - 1).  One relaxation step (section "Time
+ * Stepping") advances dx/dt = u (eq. "x integration") with the frictional
+ * velocity u = J x B (eq. "magneto friction", gamma = 1, mu_0 = 1), where
+ * B = (dx/dX) B0 / det(dx/dX) is the pull-back of the initial field
+ * (eq. "B transformation") and J = curl B comes from Stokes loops through
+ * the nearest neighbours (section "Mimetic Operators", eqs. "current
+ * discrete" to "current matrix equation") or, switchably, from direct
+ * derivatives (the classic method the paper compares against).  Nodes on
+ * the boundary are line-tied: they never move (section "Boundary
+ * Conditions").
+ *
+ * Layout.  Every nodal vector field crossing this ABI is float64, SoA:
+ * component c of node (i, j, k) at v[c*N + (k*ny + j)*nx + i],
+ * N = nx*ny*nz.
+ *
+ * Memory.  The library never allocates device memory.  The caller passes a
+ * device workspace of at least glemur_workspace_bytes() bytes (for example
+ * a torch.uint8 tensor) and keeps it alive until glemur_destroy().  Host
+ * pointers passed with GLEMUR_MEM_HOST may be pageable or pinned.
+ *
+ * Streams.  All device work runs on the cudaStream_t given to
+ * glemur_init_grid (NULL = the legacy default stream).  Calls that return
+ * host scalars (glemur_step, glemur_energy, glemur_forcefree_err,
+ * glemur_get_stats) synchronise that stream; glemur_attempts does not.
+ *
+ * Errors.  Every int-returning call returns GLEMUR_OK (0) or a negative
+ * GLEMUR_ERR_* code; glemur_strerror() names it.  After an error status
+ * from the step (COLLAPSED, NONFINITE, DT_UNDERFLOW) the context keeps the
+ * last accepted state and refuses further steps until glemur_set_x().
+ */
+#ifndef GLEMUR_H
+#define GLEMUR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum glemur_precision {
+  GLEMUR_FP64 = 0,  /* FP64 storage and arithmetic throughout */
+  GLEMUR_MIXED = 1  /* FP32 displacement, B0 and stage fields with FP32
+                       stencil arithmetic; determinants, reductions and the
+                       step-size control carried at >= 44-bit precision */
+};
+
+enum glemur_curl {
+  GLEMUR_CURL_MIMETIC = 0, /* nearest-neighbour Stokes loops (default) */
+  GLEMUR_CURL_DIRECT = 1   /* direct derivatives of B = F B0 / det F */
+};
+
+enum glemur_mem { GLEMUR_MEM_DEVICE = 0, GLEMUR_MEM_HOST = 1 };
+
+enum glemur_status {
+  GLEMUR_OK = 0,
+  GLEMUR_ERR_BADARG = -1,       /* invalid argument or context state */
+  GLEMUR_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  GLEMUR_ERR_COLLAPSED = -3,    /* det(dx/dX) <= 0 somewhere: grid folded */
+  GLEMUR_ERR_NONFINITE = -4,    /* NaN/Inf in the error estimate */
+  GLEMUR_ERR_DT_UNDERFLOW = -5, /* step shrank below dt_min or too many
+                                   consecutive rejections */
+  GLEMUR_ERR_WORKSPACE = -6     /* workspace missing, misaligned or small */
+};
+
+typedef struct glemur_ctx glemur_ctx;
+
+/* Options; glemur_default_opts() fills the defaults given here.  The paper
+ * fixes the control law dt' = dt |Lambda_0/Lambda|^0.2 (eq. "time
+ * stepping") but no tolerance, initial step or clamps. */
+typedef struct {
+  int precision;      /* glemur_precision, default GLEMUR_FP64 */
+  int curl;           /* glemur_curl, default GLEMUR_CURL_MIMETIC */
+  double lambda0;     /* Lambda_0: tolerance on the max error in x, 1e-7 */
+  double dt0;         /* first step size, 1e-3 */
+  double dt_min;      /* smallest step before GLEMUR_ERR_DT_UNDERFLOW, 1e-14 */
+  double grow_max;    /* clamp on dt'/dt when growing, 5 */
+  double shrink_min;  /* clamp on dt'/dt when shrinking, 0.1 */
+  int max_rejects;    /* consecutive rejections allowed, 64 */
+  int diag_each_attempt; /* 1: every attempt also reduces E_M and xi of the
+                            state it starts from (default 1) */
+} glemur_opts;
+
+typedef struct {
+  long long accepted;   /* accepted steps since glemur_set_x */
+  long long rejected;   /* rejected attempts since glemur_set_x */
+  double t;             /* time of the accepted state */
+  double dt;            /* step size of the next attempt */
+  double lambda;        /* error estimate Lambda of the last attempt */
+  double energy;        /* E_M of the state the last attempt started from
+                           (when diag_each_attempt is on, else 0; NaN with
+                           the direct current -- use glemur_energy) */
+  double xi;            /* xi = max |J x B| / B^2 of that state */
+  double xi_sin;        /* max |J x B| / (|J| |B|) of that state */
+  int status;           /* GLEMUR_OK or the error that stopped stepping */
+} glemur_stats;
+
+/* Fill *o with the defaults listed in glemur_opts. */
+void glemur_default_opts(glemur_opts* o);
+
+/* Device workspace needed for an nx*ny*nz grid at the given precision
+ * (bytes, a multiple of 256).  Returns 0 for invalid sizes. */
+size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
+
+/* Create a context for an nx*ny*nz node grid (each >= 3) with labels on the
+ * box [lo, hi] (hi_a > lo_a).  `opts` may be NULL for the defaults.
+ * `stream` is a cudaStream_t (or NULL).  `workspace` is caller-owned
+ * device memory of ws_bytes >= glemur_workspace_bytes(), 256-byte aligned.
+ * The positions start at x = X and B0 = 0; call glemur_set_x/glemur_set_B0.
+ * On success *out receives the context.  Errors: BADARG, WORKSPACE, CUDA. */
+int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz,
+                     const double lo[3], const double hi[3],
+                     const glemur_opts* opts, void* stream, void* workspace,
+                     size_t ws_bytes);
+
+/* Set the node positions x(X) (float64 field, layout above; `mem` says
+ * where it lives).  Boundary nodes keep these positions for ever.  Resets
+ * the step counters, the time and the error status, and sets dt = dt0.
+ * Section "Initial Configuration" (the initial grid), eq. "x integration"
+ * (x(X,0) = X unless pre-distorted). */
+int glemur_set_x(glemur_ctx* ctx, const double* x, int mem);
+
+/* Set the initial field B(X, 0) on the nodes (float64 field).  Eq. "B
+ * transformation" uses it at every step; it is not modified. */
+int glemur_set_B0(glemur_ctx* ctx, const double* B0, int mem);
+
+/* Copy the current accepted positions x into `x` (float64 field). */
+int glemur_get_x(glemur_ctx* ctx, double* x, int mem);
+
+/* Frictional velocity u = J x B of the current state at every node (0 on
+ * the boundary) into `u` (float64 field): the right-hand side of eq. "x
+ * integration" (eq. "magneto friction"). */
+int glemur_velocity(glemur_ctx* ctx, double* u, int mem);
+
+/* Advance by n_accept accepted steps (n_accept >= 0) of the Cash-Karp
+ * 5(4) scheme with the error-controlled step of section "Time Stepping":
+ * Lambda = max over nodes and components of the embedded error in x;
+ * accept iff Lambda <= Lambda_0; dt' = dt (Lambda_0/Lambda)^0.2 when
+ * rejecting (redo) or when Lambda < Lambda_0/2 (grow), clamped by
+ * shrink_min/grow_max.  An attempt whose trial stage input folds the grid
+ * (det dx/dX <= 0) is rejected with the largest shrink; a folded accepted
+ * state stops with COLLAPSED.  Synchronises; fills *stats when non-NULL.
+ * Errors: BADARG, CUDA, COLLAPSED, NONFINITE, DT_UNDERFLOW. */
+int glemur_step(glemur_ctx* ctx, int n_accept, glemur_stats* stats);
+
+/* Enqueue exactly n_attempts Cash-Karp attempts with the same control law
+ * (each either accepted or rejected) without synchronising.  Throughput
+ * harnesses time this; read the outcome with glemur_get_stats. */
+int glemur_attempts(glemur_ctx* ctx, int n_attempts);
+
+/* One attempt of the given size that is always accepted (replays a
+ * recorded step-size schedule; section "Time Stepping" without the
+ * control).  The next automatic step starts from dt.  Synchronises. */
+int glemur_step_fixed(glemur_ctx* ctx, double dt, glemur_stats* stats);
+
+/* Magnetic energy E_M = 1/2 sum zeta B^2 Delta dX dY dZ of the current
+ * state (eq. "magnetic energy"; zeta = 1, 1/2, 1/4, 1/8 inside, on faces,
+ * edges, corners).  FP64 accumulation.  Synchronises. */
+int glemur_energy(glemur_ctx* ctx, double* E);
+
+/* Force-free errors of the current state over interior nodes:
+ * *xi = max |J x B| / B^2 (section "Evolution of Diagnostic Parameters")
+ * and *xi_sin = max |J x B| / (|J| |B|) (nodes with |J||B| = 0 skipped),
+ * with the context's current.  Synchronises. */
+int glemur_forcefree_err(glemur_ctx* ctx, double* xi, double* xi_sin);
+
+/* Counters and last-attempt values (see glemur_stats).  Synchronises. */
+int glemur_get_stats(glemur_ctx* ctx, glemur_stats* stats);
+
+/* Number of CUDA kernels one attempt launches (for launch accounting). */
+int glemur_kernels_per_attempt(const glemur_ctx* ctx);
+
+/* Enqueue one attempt exactly as glemur_attempts(ctx, 1) does, with a CUDA
+ * event recorded on the context's stream before each of its kernels and
+ * after the last; synchronise and write the kernels' durations in
+ * milliseconds to ms[0 .. n-1] in launch order (Cash-Karp stages 1..6, then
+ * the step control), n = glemur_kernels_per_attempt(ctx) <= cap.  Returns n,
+ * or a negative error (BADARG if cap < n). */
+int glemur_profile_attempt(glemur_ctx* ctx, float* ms, int cap);
+
+/* Release the context (host memory only; the workspace stays the
+ * caller's). NULL is ignored. */
+void glemur_destroy(glemur_ctx* ctx);
+
+/* Static description of a status code. */
+const char* glemur_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLEMUR_H */

@@ -16,6 +16,7 @@
  */
 #include "glemur_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -155,7 +156,7 @@ static int pullback_at(const ora_grid* g, const double* x, const double* B0,
     B[a] = (F[a * 3 + 0] * b0[0] + F[a * 3 + 1] * b0[1] +
             F[a * 3 + 2] * b0[2]) / D;
   if (Delta) *Delta = D;
-  return D > 0.0 ? ORA_OK : ORA_ERR_COLLAPSED;
+  return D <= 0.0 ? ORA_ERR_COLLAPSED : ORA_OK; /* NaN: left to the error norm */
 }
 
 int ora_pullback(const ora_grid* g, const double* x, const double* B0,
@@ -369,7 +370,7 @@ static int direct_at(const ora_grid* g, const double* x, const double* B0,
   cross(r2, r0, &cof[3]);
   cross(r0, r1, &cof[6]);
   double D = det3(F);
-  if (!(D > 0.0)) return ORA_ERR_COLLAPSED;
+  if (D <= 0.0) return ORA_ERR_COLLAPSED;
   double W[3];
   for (int a = 0; a < 3; ++a)
     W[a] = F[a * 3 + 0] * b0c[0] + F[a * 3 + 1] * b0c[1] + F[a * 3 + 2] * b0c[2];
@@ -605,6 +606,19 @@ static int grid_rhs(void* vctx, const double* y, double* dydt) {
   return ora_velocity(c->g, c->curl, y, c->B0, dydt);
 }
 
+/* ORA_ERR_COLLAPSED if det(dx/dX) <= 0 at some node of x. */
+static int pullback_status(const ora_grid* g, const double* x,
+                           const double* B0) {
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        double b[3];
+        if (pullback_at(g, x, B0, i, j, k, b, NULL) != ORA_OK)
+          return ORA_ERR_COLLAPSED;
+      }
+  return ORA_OK;
+}
+
 static double max_abs(long n, const double* v) {
   double m = 0.0;
   for (long i = 0; i < n; ++i) {
@@ -649,11 +663,22 @@ int ora_relax(const ora_grid* g, int curl, const ora_control_opts* o,
   double t = st ? st->t : 0.0, lam = 0.0;
   while (acc < n_accept) {
     rc = ora_ck_attempt(n, x, *dt, grid_rhs, &c, xn, er, NULL);
-    if (rc != ORA_OK) break;
-    lam = max_abs(n, er); /* Lambda: maximum error in x */
     double dt_next;
     int accept;
-    rc = ora_step_control(o, lam, *dt, consec, &dt_next, &accept);
+    if (rc == ORA_ERR_COLLAPSED) {
+      /* A stage input folded the grid.  If the accepted state itself is
+       * folded the run cannot continue; otherwise the attempt is rejected
+       * with the largest shrink (its error is unbounded), which is how the
+       * step size collapses before a blow-up (section "Grid Convexity and
+       * Stability"). */
+      if (pullback_status(g, x, B0) != ORA_OK) break;
+      lam = INFINITY;
+      rc = ora_step_control(o, DBL_MAX, *dt, consec, &dt_next, &accept);
+    } else {
+      if (rc != ORA_OK) break;
+      lam = max_abs(n, er); /* Lambda: maximum error in x */
+      rc = ora_step_control(o, lam, *dt, consec, &dt_next, &accept);
+    }
     if (rc != ORA_OK) {
       if (!accept) ++rej;
       break;

@@ -1,0 +1,735 @@
+// Host side of the C ABI declared in include/glemur.h: context, workspace
+// layout, the attempt loop with device-side step control, diagnostics and
+// the layout conversions at the boundary.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "glemur.h"
+#include "glemur_dev.cuh"
+
+namespace glemur {
+cudaError_t prepare_stage_f64();
+cudaError_t prepare_stage_f32();
+int stage_ctas_per_sm_f64(int curl);
+int stage_ctas_per_sm_f32(int curl);
+cudaError_t launch_stage_f64(const StageArgs<double>& a, int curl, bool final_stage,
+                             dim3 grid, cudaStream_t s);
+cudaError_t launch_stage_f32(const StageArgs<float>& a, int curl, bool final_stage,
+                             dim3 grid, cudaStream_t s);
+
+// Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
+// of section "Time Stepping".
+__constant__ double CK_A[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0, 0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0, 0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0,
+     253.0 / 4096.0, 0}};
+__constant__ double CK_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0,
+                                512.0 / 1771.0};
+__constant__ double CK_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0,
+                                13525.0 / 55296.0, 277.0 / 14336.0, 1.0 / 4.0};
+
+// dt-scaled coefficients of the pending attempt.
+__device__ void set_coeffs(DevState* st) {
+  const double dt = st->dt;
+  for (int s = 0; s < 6; ++s) {
+    for (int j = 0; j < 6; ++j) {
+      st->dta[s][j] = dt * CK_A[s][j];
+      st->dtaf[s][j] = (float)st->dta[s][j];
+    }
+    st->dtb[s] = dt * CK_B5[s];
+    st->dte[s] = dt * (CK_B5[s] - CK_B4[s]);
+    st->dtbf[s] = (float)st->dtb[s];
+    st->dtef[s] = (float)st->dte[s];
+  }
+}
+
+__global__ void k_reset_state(DevState* st, double dt0, double lambda0, double dt_min,
+                              double grow_max, double shrink_min, int max_rejects) {
+  st->dt = dt0;
+  st->t = 0.0;
+  st->lambda = 0.0;
+  st->lambda0 = lambda0;
+  st->dt_min = dt_min;
+  st->grow_max = grow_max;
+  st->shrink_min = shrink_min;
+  st->n_accept = 0;
+  st->n_reject = 0;
+  st->target = 0;
+  st->consec = 0;
+  st->cur = 0;
+  st->status = ST_OK;
+  st->flags = 0;
+  st->max_rejects = max_rejects;
+  st->replay = 0;
+  st->E = st->xi = st->xi_sin = 0.0;
+  set_coeffs(st);
+}
+
+__global__ void k_set_target(DevState* st, long long extra, int relative) {
+  st->target = relative ? st->n_accept + extra : extra;
+}
+
+__global__ void k_set_dt(DevState* st, double dt, int replay) {
+  st->dt = dt;
+  st->replay = replay;
+  st->target = st->n_accept + 1;
+  set_coeffs(st);
+}
+
+// Sum and max reductions of the per-CTA diagnostic partials (fixed order).
+__device__ void finalize_diag(DevState* st, const double* part, int nb, double* sh) {
+  double e = 0.0, x2 = 0.0, xs2 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    e += part[PART_E * nb + b];
+    x2 = nanmax(x2, part[PART_XI2 * nb + b]);
+    xs2 = nanmax(xs2, part[PART_XIS2 * nb + b]);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    x2 = nanmax(x2, __shfl_xor_sync(0xffffffffu, x2, o));
+    xs2 = nanmax(xs2, __shfl_xor_sync(0xffffffffu, xs2, o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[w] = e;
+    sh[32 + w] = x2;
+    sh[64 + w] = xs2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double E = 0.0, X = 0.0, XS = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      E += sh[i];
+      X = nanmax(X, sh[32 + i]);
+      XS = nanmax(XS, sh[64 + i]);
+    }
+    st->E = E / 16.0;  // eq. "magnetic energy" in index-space units
+    st->xi = sqrt(X);
+    st->xi_sin = sqrt(XS);
+  }
+}
+
+__global__ void k_diag_finalize(DevState* st, const double* part, int nb) {
+  __shared__ double sh[96];
+  finalize_diag(st, part, nb, sh);
+}
+
+// Eq. "time stepping" and the acceptance rule around it, after each attempt.
+__global__ void k_control(DevState* st, const double* part, int nb, int diag) {
+  if (st->status != ST_OK || st->n_accept >= st->target) return;
+  __shared__ double sh[96];
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = nanmax(m, part[PART_LAMBDA * nb + b]);
+  for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = nanmax(m, sh[i]);
+    sh[95] = m;
+  }
+  __syncthreads();
+  if (diag) finalize_diag(st, part, nb, sh);
+  if (threadIdx.x != 0) return;
+  const double lam = sh[95];
+  const double dt = st->dt;
+  st->lambda = lam;
+  if (st->flags & FLAG_COLLAPSED) {
+    st->status = ST_COLLAPSED;
+    st->n_reject++;
+    return;
+  }
+  const bool folded = (st->flags & FLAG_FOLDED_TRIAL) != 0;
+  if (!folded && !isfinite(lam)) {
+    st->status = ST_NONFINITE;
+    st->n_reject++;
+    return;
+  }
+  bool accept;
+  double dtn;
+  if (folded) {
+    // a trial stage folded the grid: reject with the largest shrink
+    accept = false;
+    dtn = dt * st->shrink_min;
+    st->lambda = INFINITY;
+    if (st->consec + 1 > st->max_rejects || dtn < st->dt_min) {
+      st->status = ST_DT_UNDERFLOW;
+      st->n_reject++;
+      st->consec++;
+      return;
+    }
+  } else if (st->replay) {
+    accept = true;
+    dtn = dt;
+    st->replay = 0;
+  } else if (lam > st->lambda0) {
+    double fac = pow(st->lambda0 / lam, 0.2);
+    if (fac < st->shrink_min) fac = st->shrink_min;
+    accept = false;
+    dtn = dt * fac;
+    if (st->consec + 1 > st->max_rejects || dtn < st->dt_min) {
+      st->status = ST_DT_UNDERFLOW;
+      st->n_reject++;
+      st->consec++;
+      return;
+    }
+  } else {
+    accept = true;
+    double fac = 1.0;
+    if (lam < 0.5 * st->lambda0) {
+      fac = lam > 0.0 ? pow(st->lambda0 / lam, 0.2) : st->grow_max;
+      if (fac > st->grow_max) fac = st->grow_max;
+    }
+    dtn = dt * fac;
+  }
+  if (accept) {
+    st->t += dt;
+    st->cur ^= 1;
+    st->n_accept++;
+    st->consec = 0;
+  } else {
+    st->n_reject++;
+    st->consec++;
+  }
+  st->dt = dtn;
+  st->flags = 0;
+  set_coeffs(st);
+}
+
+// ---- layout conversions at the boundary (float64 SoA fields) ----------
+
+struct GridGeom {
+  int nx, ny, nz;
+  double lo[3], h[3];
+};
+
+__device__ __forceinline__ double label(const GridGeom& g, int a, int i) {
+  return g.lo[a] + (double)i * g.h[a];
+}
+
+template <typename T>
+__global__ void k_set_x(GridGeom g, const double* __restrict__ x, T* d0, T* d1) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+    const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, k)};
+    for (int c = 0; c < 3; ++c) {
+      const T v = (T)(x[c * N + n] - X[c]);
+      d0[c * N + n] = v;
+      d1[c * N + n] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_get_x(GridGeom g, const T* const* dbuf, const DevState* st,
+                        double* __restrict__ x) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  const T* d = dbuf[st->cur];
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+    const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, k)};
+    for (int c = 0; c < 3; ++c) x[c * N + n] = X[c] + (double)d[c * N + n];
+  }
+}
+
+template <typename T>
+__global__ void k_set_B0(GridGeom g, const double* __restrict__ B0, T* B0s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  // B0s_a = B0_a * 4 h_{a+1} h_{a+2}
+  const double s[3] = {4.0 * g.h[1] * g.h[2], 4.0 * g.h[2] * g.h[0], 4.0 * g.h[0] * g.h[1]};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x)
+    for (int c = 0; c < 3; ++c) B0s[c * N + n] = (T)(B0[c * N + n] * s[c]);
+}
+
+template <typename T>
+__global__ void k_to_f64(long long M, const T* __restrict__ src, double* __restrict__ dst) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < M;
+       n += (long long)gridDim.x * blockDim.x)
+    dst[n] = (double)src[n];
+}
+
+}  // namespace glemur
+
+using namespace glemur;
+
+struct glemur_ctx {
+  int nx, ny, nz;
+  long long N;
+  double lo[3], hi[3], h[3];
+  glemur_opts o;
+  cudaStream_t s;
+  unsigned char* ws;
+  size_t ws_bytes;
+  size_t esize;     // bytes per stored scalar (8 or 4)
+  void* dbuf[2];
+  void** dbuf_dev;  // device copy of {dbuf[0], dbuf[1]}
+  void* B0s;
+  void* k[5];
+  double* stage;    // 3N doubles for host transfers
+  double* part;     // NPART * max_blocks
+  DevState* st;
+  int max_blocks, nblocks, kz;
+  dim3 grid;
+  int nsm;
+};
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t field, stage, part, state, ptrs, total;
+  int max_blocks;
+};
+
+bool valid_dims(int nx, int ny, int nz) {
+  return nx >= 3 && ny >= 3 && nz >= 3 && (long long)nx * ny * nz <= (1LL << 40);
+}
+
+Layout layout(int nx, int ny, int nz, int precision) {
+  Layout L{};
+  const long long N = (long long)nx * ny * nz;
+  const size_t es = precision == GLEMUR_MIXED ? 4 : 8;
+  L.field = align256((size_t)(3 * N) * es);
+  L.stage = align256((size_t)(3 * N) * sizeof(double));
+  const long long gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
+  L.max_blocks = (int)(gx * gy * nz);
+  L.part = align256((size_t)NPART * L.max_blocks * sizeof(double));
+  L.state = align256(sizeof(DevState));
+  L.ptrs = 256;
+  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs;
+  return L;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA; }
+
+GridGeom geom(const glemur_ctx* c) {
+  GridGeom g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nz = c->nz;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = c->lo[a];
+    g.h[a] = c->h[a];
+  }
+  return g;
+}
+
+int elementwise_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+// Planes per CTA: minimise (waves) x (planes + 2 halo planes) per CTA.
+int choose_kz(int nz, int gxy, int cap) {
+  const char* env = getenv("GLEMUR_KZ");
+  if (env && atoi(env) > 0) return atoi(env) < nz ? atoi(env) : nz;
+  if (cap < 1) cap = 1;
+  int best = nz;
+  double best_cost = 1e300;
+  for (int kz = 1; kz <= nz; ++kz) {
+    const long long ctas = (long long)gxy * ((nz + kz - 1) / kz);
+    const double waves = (double)((ctas + cap - 1) / cap);
+    const double cost = waves * (kz + 2);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = kz;
+    }
+  }
+  return best;
+}
+
+template <typename T>
+StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
+  StageArgs<T> a;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.kz = c->kz;
+  for (int i = 0; i < 3; ++i) a.h2[i] = 2.0 * c->h[i];
+  a.d[0] = (const T*)c->dbuf[0];
+  a.d[1] = (const T*)c->dbuf[1];
+  a.B0s = (const T*)c->B0s;
+  for (int j = 0; j < 5; ++j) a.k[j] = (T*)c->k[j];
+  a.stage = stage;
+  a.diag = diag;
+  a.force = force;
+  a.st = c->st;
+  a.part = c->part;
+  a.nblocks = c->nblocks;
+  return a;
+}
+
+cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force) {
+  const bool fin = stage == 5;
+  if (c->o.precision == GLEMUR_MIXED)
+    return launch_stage_f32(make_args<float>(c, stage, diag, force), curl, fin, c->grid, c->s);
+  return launch_stage_f64(make_args<double>(c, stage, diag, force), curl, fin, c->grid, c->s);
+}
+
+cudaError_t launch_attempt(const glemur_ctx* c) {
+  const int diag = c->o.diag_each_attempt ? 1 : 0;
+  for (int s = 0; s < 6; ++s) {
+    cudaError_t e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
+    if (e != cudaSuccess) return e;
+  }
+  k_control<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks, diag);
+  return cudaGetLastError();
+}
+
+int read_state(glemur_ctx* c, DevState* hs) {
+  cudaError_t e = cudaMemcpyAsync(hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  return cuda_rc(e);
+}
+
+void fill_stats(const DevState& hs, int curl, glemur_stats* out) {
+  if (!out) return;
+  out->accepted = hs.n_accept;
+  out->rejected = hs.n_reject;
+  out->t = hs.t;
+  out->dt = hs.dt;
+  out->lambda = hs.lambda;
+  // the direct-current kernel visits interior nodes only: no per-attempt E_M
+  out->energy = curl == GLEMUR_CURL_DIRECT ? NAN : hs.E;
+  out->xi = hs.xi;
+  out->xi_sin = hs.xi_sin;
+  out->status = hs.status;
+}
+
+int reset_state(glemur_ctx* c) {
+  k_reset_state<<<1, 1, 0, c->s>>>(c->st, c->o.dt0, c->o.lambda0, c->o.dt_min, c->o.grow_max,
+                                   c->o.shrink_min, c->o.max_rejects);
+  return cuda_rc(cudaGetLastError());
+}
+
+// Source pointer of an input field: the caller's device pointer, or the
+// staging buffer after an H2D copy.
+int stage_in(glemur_ctx* c, const double* src, int mem, const double** dev) {
+  if (!src) return GLEMUR_ERR_BADARG;
+  if (mem == GLEMUR_MEM_DEVICE) {
+    *dev = src;
+    return GLEMUR_OK;
+  }
+  if (mem != GLEMUR_MEM_HOST) return GLEMUR_ERR_BADARG;
+  cudaError_t e = cudaMemcpyAsync(c->stage, src, sizeof(double) * 3 * c->N,
+                                  cudaMemcpyHostToDevice, c->s);
+  *dev = c->stage;
+  return cuda_rc(e);
+}
+
+int stage_out(glemur_ctx* c, double* dst, int mem) {
+  if (mem == GLEMUR_MEM_DEVICE) return GLEMUR_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, c->stage, sizeof(double) * 3 * c->N,
+                                  cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  return cuda_rc(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void glemur_default_opts(glemur_opts* o) {
+  if (!o) return;
+  o->precision = GLEMUR_FP64;
+  o->curl = GLEMUR_CURL_MIMETIC;
+  o->lambda0 = 1e-7;
+  o->dt0 = 1e-3;
+  o->dt_min = 1e-14;
+  o->grow_max = 5.0;
+  o->shrink_min = 0.1;
+  o->max_rejects = 64;
+  o->diag_each_attempt = 1;
+}
+
+size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision) {
+  if (!valid_dims(nx, ny, nz)) return 0;
+  if (precision != GLEMUR_FP64 && precision != GLEMUR_MIXED) return 0;
+  return layout(nx, ny, nz, precision).total;
+}
+
+int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3],
+                     const double hi[3], const glemur_opts* opts, void* stream,
+                     void* workspace, size_t ws_bytes) {
+  if (!out || !lo || !hi || !valid_dims(nx, ny, nz)) return GLEMUR_ERR_BADARG;
+  *out = nullptr;
+  glemur_opts o;
+  glemur_default_opts(&o);
+  if (opts) o = *opts;
+  if ((o.precision != GLEMUR_FP64 && o.precision != GLEMUR_MIXED) ||
+      (o.curl != GLEMUR_CURL_MIMETIC && o.curl != GLEMUR_CURL_DIRECT) ||
+      !(o.lambda0 > 0) || !(o.dt0 > 0) || !(o.dt_min >= 0) || !(o.grow_max >= 1) ||
+      !(o.shrink_min > 0 && o.shrink_min <= 1) || o.max_rejects < 0)
+    return GLEMUR_ERR_BADARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(hi[a] > lo[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a]))
+      return GLEMUR_ERR_BADARG;
+  const Layout L = layout(nx, ny, nz, o.precision);
+  if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace & 255))
+    return GLEMUR_ERR_WORKSPACE;
+  glemur_ctx* c = new (std::nothrow) glemur_ctx();
+  if (!c) return GLEMUR_ERR_BADARG;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->N = (long long)nx * ny * nz;
+  const int n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    c->lo[a] = lo[a];
+    c->hi[a] = hi[a];
+    c->h[a] = (hi[a] - lo[a]) / (n[a] - 1);
+  }
+  c->o = o;
+  c->s = (cudaStream_t)stream;
+  c->ws = (unsigned char*)workspace;
+  c->ws_bytes = ws_bytes;
+  c->esize = o.precision == GLEMUR_MIXED ? 4 : 8;
+  unsigned char* p = c->ws;
+  c->dbuf[0] = p; p += L.field;
+  c->dbuf[1] = p; p += L.field;
+  c->B0s = p; p += L.field;
+  for (int j = 0; j < 5; ++j) { c->k[j] = p; p += L.field; }
+  c->stage = (double*)p; p += L.stage;
+  c->part = (double*)p; p += L.part;
+  c->st = (DevState*)p; p += L.state;
+  c->dbuf_dev = (void**)p;
+  c->max_blocks = L.max_blocks;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = o.precision == GLEMUR_MIXED ? prepare_stage_f32() : prepare_stage_f64();
+  if (e != cudaSuccess) {
+    delete c;
+    return GLEMUR_ERR_CUDA;
+  }
+  const int per_sm = o.precision == GLEMUR_MIXED ? stage_ctas_per_sm_f32(o.curl)
+                                                  : stage_ctas_per_sm_f64(o.curl);
+  const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
+  c->kz = choose_kz(nz, gx * gy, per_sm * c->nsm);
+  c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
+  c->nblocks = gx * gy * (int)c->grid.z;
+
+  // zero displacement (x = X), B0 and stage fields; boundary entries of the
+  // stage fields stay zero for ever (line-tied nodes do not move)
+  e = cudaMemsetAsync(c->ws, 0, 8 * L.field + L.stage + L.part, c->s);
+  void* ptrs[2] = {c->dbuf[0], c->dbuf[1]};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->dbuf_dev, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess || reset_state(c) != GLEMUR_OK) {
+    delete c;
+    return GLEMUR_ERR_CUDA;
+  }
+  *out = c;
+  return GLEMUR_OK;
+}
+
+int glemur_set_x(glemur_ctx* c, const double* x, int mem) {
+  if (!c) return GLEMUR_ERR_BADARG;
+  const double* src = nullptr;
+  int rc = stage_in(c, x, mem, &src);
+  if (rc) return rc;
+  const int nb = elementwise_blocks(c->N);
+  if (c->o.precision == GLEMUR_MIXED)
+    k_set_x<float><<<nb, 256, 0, c->s>>>(geom(c), src, (float*)c->dbuf[0], (float*)c->dbuf[1]);
+  else
+    k_set_x<double><<<nb, 256, 0, c->s>>>(geom(c), src, (double*)c->dbuf[0],
+                                          (double*)c->dbuf[1]);
+  rc = cuda_rc(cudaGetLastError());
+  if (rc) return rc;
+  return reset_state(c);
+}
+
+int glemur_set_B0(glemur_ctx* c, const double* B0, int mem) {
+  if (!c) return GLEMUR_ERR_BADARG;
+  const double* src = nullptr;
+  int rc = stage_in(c, B0, mem, &src);
+  if (rc) return rc;
+  const int nb = elementwise_blocks(c->N);
+  if (c->o.precision == GLEMUR_MIXED)
+    k_set_B0<float><<<nb, 256, 0, c->s>>>(geom(c), src, (float*)c->B0s);
+  else
+    k_set_B0<double><<<nb, 256, 0, c->s>>>(geom(c), src, (double*)c->B0s);
+  return cuda_rc(cudaGetLastError());
+}
+
+int glemur_get_x(glemur_ctx* c, double* x, int mem) {
+  if (!c || !x || (mem != GLEMUR_MEM_DEVICE && mem != GLEMUR_MEM_HOST)) return GLEMUR_ERR_BADARG;
+  double* dst = mem == GLEMUR_MEM_DEVICE ? x : c->stage;
+  const int nb = elementwise_blocks(c->N);
+  if (c->o.precision == GLEMUR_MIXED)
+    k_get_x<float><<<nb, 256, 0, c->s>>>(geom(c), (const float* const*)c->dbuf_dev, c->st, dst);
+  else
+    k_get_x<double><<<nb, 256, 0, c->s>>>(geom(c), (const double* const*)c->dbuf_dev, c->st,
+                                          dst);
+  int rc = cuda_rc(cudaGetLastError());
+  if (rc) return rc;
+  return stage_out(c, x, mem);
+}
+
+int glemur_velocity(glemur_ctx* c, double* u, int mem) {
+  if (!c || !u || (mem != GLEMUR_MEM_DEVICE && mem != GLEMUR_MEM_HOST)) return GLEMUR_ERR_BADARG;
+  cudaError_t e = launch_stage(c, c->o.curl, 0, 0, 1);
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  double* dst = mem == GLEMUR_MEM_DEVICE ? u : c->stage;
+  const long long M = 3 * c->N;
+  if (c->o.precision == GLEMUR_MIXED)
+    k_to_f64<float><<<elementwise_blocks(M), 256, 0, c->s>>>(M, (const float*)c->k[0], dst);
+  else
+    k_to_f64<double><<<elementwise_blocks(M), 256, 0, c->s>>>(M, (const double*)c->k[0], dst);
+  int rc = cuda_rc(cudaGetLastError());
+  if (rc) return rc;
+  return stage_out(c, u, mem);
+}
+
+int glemur_attempts(glemur_ctx* c, int n_attempts) {
+  if (!c || n_attempts < 0) return GLEMUR_ERR_BADARG;
+  k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
+  cudaError_t e = cudaGetLastError();
+  for (int i = 0; i < n_attempts && e == cudaSuccess; ++i) e = launch_attempt(c);
+  return cuda_rc(e);
+}
+
+int glemur_step(glemur_ctx* c, int n_accept, glemur_stats* stats) {
+  if (!c || n_accept < 0) return GLEMUR_ERR_BADARG;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  if (hs.status != ST_OK) {
+    fill_stats(hs, c->o.curl, stats);
+    return hs.status;
+  }
+  const long long target = hs.n_accept + n_accept;
+  k_set_target<<<1, 1, 0, c->s>>>(c->st, target, 0);
+  if ((rc = cuda_rc(cudaGetLastError()))) return rc;
+  while (hs.n_accept < target) {
+    const long long remaining = target - hs.n_accept;
+    for (long long i = 0; i < remaining; ++i)
+      if ((rc = cuda_rc(launch_attempt(c)))) return rc;
+    if ((rc = read_state(c, &hs))) return rc;
+    if (hs.status != ST_OK) break;
+  }
+  fill_stats(hs, c->o.curl, stats);
+  return hs.status;
+}
+
+int glemur_step_fixed(glemur_ctx* c, double dt, glemur_stats* stats) {
+  if (!c || !(dt > 0) || !std::isfinite(dt)) return GLEMUR_ERR_BADARG;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  if (hs.status != ST_OK) {
+    fill_stats(hs, c->o.curl, stats);
+    return hs.status;
+  }
+  k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 1);
+  if ((rc = cuda_rc(cudaGetLastError()))) return rc;
+  if ((rc = cuda_rc(launch_attempt(c)))) return rc;
+  if ((rc = read_state(c, &hs))) return rc;
+  fill_stats(hs, c->o.curl, stats);
+  return hs.status;
+}
+
+int glemur_energy(glemur_ctx* c, double* E) {
+  if (!c || !E) return GLEMUR_ERR_BADARG;
+  cudaError_t e = launch_stage(c, GLEMUR_CURL_MIMETIC, 0, 1, 1);
+  if (e == cudaSuccess) {
+    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  *E = hs.E;
+  return GLEMUR_OK;
+}
+
+int glemur_forcefree_err(glemur_ctx* c, double* xi, double* xi_sin) {
+  if (!c || !xi || !xi_sin) return GLEMUR_ERR_BADARG;
+  cudaError_t e = launch_stage(c, c->o.curl, 0, 1, 1);
+  if (e == cudaSuccess) {
+    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  *xi = hs.xi;
+  *xi_sin = hs.xi_sin;
+  return GLEMUR_OK;
+}
+
+int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
+  if (!c || !stats) return GLEMUR_ERR_BADARG;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  fill_stats(hs, c->o.curl, stats);
+  return GLEMUR_OK;
+}
+
+int glemur_kernels_per_attempt(const glemur_ctx* c) { return c ? 7 : 0; }
+
+int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
+  const int nk = glemur_kernels_per_attempt(c);
+  if (!c || !ms || cap < nk) return GLEMUR_ERR_BADARG;
+  cudaEvent_t ev[8];
+  int made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made < nk + 1 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < made - 1; ++i) cudaEventDestroy(ev[i]);
+    return GLEMUR_ERR_CUDA;
+  }
+  k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
+  e = cudaGetLastError();
+  const int diag = c->o.diag_each_attempt ? 1 : 0;
+  for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
+    e = cudaEventRecord(ev[s], c->s);
+    if (e == cudaSuccess) e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
+  if (e == cudaSuccess) {
+    k_control<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks, diag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
+  for (int i = 0; i < nk && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < nk + 1; ++i) cudaEventDestroy(ev[i]);
+  return e == cudaSuccess ? nk : GLEMUR_ERR_CUDA;
+}
+
+void glemur_destroy(glemur_ctx* c) { delete c; }
+
+const char* glemur_strerror(int status) {
+  switch (status) {
+    case GLEMUR_OK: return "ok";
+    case GLEMUR_ERR_BADARG: return "invalid argument";
+    case GLEMUR_ERR_CUDA: return "CUDA runtime error";
+    case GLEMUR_ERR_COLLAPSED: return "grid collapsed (det dx/dX <= 0)";
+    case GLEMUR_ERR_NONFINITE: return "non-finite error estimate";
+    case GLEMUR_ERR_DT_UNDERFLOW: return "step size underflow / too many rejections";
+    case GLEMUR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

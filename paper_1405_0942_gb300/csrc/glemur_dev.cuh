@@ -1,0 +1,97 @@
+// Device-side definitions shared by the GB300 kernels of the relaxation step.
+//
+// Storage.  The library keeps the displacement d = x - X (X the label grid)
+// rather than x: every stencil only needs differences of x, and
+// x(m + e_a) - x(m - e_a) = d(m + e_a) - d(m - e_a) + 2 h_a e_a, so X never
+// has to be formed and FP32 storage (mixed mode) keeps its precision in the
+// part that moves.  B0 is stored pre-scaled, B0s_a = B0_a * 4 h_{a+1} h_{a+2},
+// so that with the index-space differences g_a = 2 h_a dx/dX_a the pull-back
+// of eq. "B transformation" is B = (g_0 B0s_0 + g_1 B0s_1 + g_2 B0s_2)/det G
+// (the h factors cancel), and E_M = sum zeta |B|^2 det G / 16.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace glemur {
+
+// CTA tile: TX x TY output columns, marching in z.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NT = TX * TY;
+// Displacement tile with a halo of 2 (the mimetic current needs B at the
+// six neighbours, and B at a node needs x at its own neighbours).
+constexpr int XW = TX + 4, XH = TY + 4, XP = XW * XH;
+// B tile with a halo of 1.
+constexpr int BW = TX + 2, BH = TY + 2, BP = BW * BH;
+// Displacement tile with a halo of 1 (direct current).
+constexpr int DW = TX + 2, DH = TY + 2, DP = DW * DH;
+
+// Error flags raised by the stage kernels: det G <= 0 in the accepted state
+// (stage 1 input: fatal) or in a trial stage input (the attempt is
+// rejected with the largest shrink).
+constexpr unsigned FLAG_COLLAPSED = 1u;
+constexpr unsigned FLAG_FOLDED_TRIAL = 2u;
+
+// Device status codes (same values as glemur_status).
+constexpr int ST_OK = 0;
+constexpr int ST_COLLAPSED = -3;
+constexpr int ST_NONFINITE = -4;
+constexpr int ST_DT_UNDERFLOW = -5;
+
+// Control state of the time integration, resident in the workspace.  The
+// step-control kernel updates it after every attempt, so the host never has
+// to synchronise between attempts.
+struct DevState {
+  double dt;          // step size of the next attempt
+  double t;           // time of the accepted state
+  double lambda;      // error estimate of the last attempt
+  double lambda0, dt_min, grow_max, shrink_min;
+  long long n_accept, n_reject;
+  long long target;   // attempts stop (no-op) once n_accept reaches this
+  int consec;         // consecutive rejections
+  int cur;            // which displacement buffer holds the accepted state
+  int status;         // ST_OK or an error status
+  unsigned flags;     // FLAG_* raised by stage kernels in this attempt
+  int max_rejects;
+  int replay;         // 1: accept the next attempt whatever its error
+  // dt-scaled Cash-Karp coefficients of the pending attempt
+  double dta[6][6];
+  double dtb[6];
+  double dte[6];
+  float dtaf[6][6];
+  float dtbf[6];
+  float dtef[6];
+  // diagnostics reduced from the state the last diagnostic launch saw
+  double E, xi, xi_sin;
+};
+
+// Partial-result slots per CTA (see StageArgs::part).
+enum { PART_LAMBDA = 0, PART_E = 1, PART_XI2 = 2, PART_XIS2 = 3, NPART = 4 };
+
+template <typename T>
+struct StageArgs {
+  int nx, ny, nz;
+  int kz;              // planes per CTA along z
+  double h2[3];        // 2 h_a
+  const T* d[2];       // ping-pong displacement buffers (3N each)
+  const T* B0s;        // pre-scaled B0 (3N)
+  T* k[5];             // stage derivatives k1..k5 (3N each)
+  int stage;           // 0..5 (stage s+1 of Cash-Karp)
+  int diag;            // reduce E_M / xi partials in this launch
+  int force;           // run even if the step target is reached
+  DevState* st;
+  double* part;        // [NPART][nblocks] per-CTA partials
+  int nblocks;
+};
+
+__device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {
+  return ((long long)k * ny + j) * nx + i;
+}
+
+// max that propagates NaN: the result is NaN if either input is.
+__device__ __forceinline__ double nanmax(double a, double b) {
+  return (a > b || a != a) ? a : b;
+}
+
+}  // namespace glemur

@@ -1,0 +1,544 @@
+// Fused Cash-Karp stage kernels for the Lagrangian magneto-frictional step.
+//
+// One launch evaluates one Runge-Kutta stage k_s = u(x_s) at every interior
+// node (section "Time Stepping"; eq. "x integration" with u = J x B of eq.
+// "magneto friction").  Per CTA: a TX x TY column tile that marches along z.
+// Each z-plane of the stage input x_s = x + dt sum_{j<s} a_sj k_j is formed
+// once in shared memory (tile + halo), B = G B0s / det G (eq. "B
+// transformation", index-space form, see glemur_dev.cuh) is formed once per
+// node of the tile + halo 1, and the current and velocity are evaluated at
+// the tile's own nodes.  The last stage also forms the fifth-order update
+// and the embedded error, and reduces the CTA's max error (the Lambda of eq.
+// "time stepping").
+//
+// Mimetic current (section "Mimetic Operators").  With the index-space
+// differences g_a = x(m + e_a) - x(m - e_a) and P_a = B(m + e_a) - B(m - e_a)
+// the loop of eq. "current discrete" through the neighbours +e_p, +e_q, -e_p,
+// -e_q has circulation (P_p . g_q - P_q . g_p) / 2 and the vector area of
+// eq. "sum of triangles" is (g_p x g_q) / 2.  The three loop equations of
+// eq. "current matrix equation", J . (g_p x g_q) = P_p . g_q - P_q . g_p for
+// (p, q) = (1, 2), (2, 0), (0, 1), have the matrix of rows g_p x g_q =
+// det(G) G^-1, so their solution is J = (c_0 g_0 + c_1 g_1 + c_2 g_2) / det G
+// with c_r the right-hand sides: the same J as the paper's loop form, with
+// no 3x3 solve and det G the one the pull-back already needs.
+//
+// Direct current (the classic method).  dB/dX follows from B = G B0s / det G
+// by the product rule with second differences of x, differences of B0s and
+// Jacobi's formula for d det G; dB/dx = dB/dX G^-1 (index-space scaling
+// cancels) and J = curl_x B.
+#pragma once
+
+#include "glemur_dev.cuh"
+
+namespace glemur {
+
+// ------------------------------------------------------------ arithmetic
+
+// Determinant of G = [g0 g1 g2] (columns).
+__device__ __forceinline__ double det3(const double g0[3], const double g1[3],
+                                       const double g2[3]) {
+  double m0 = g1[1] * g2[2] - g1[2] * g2[1];
+  double m1 = g1[2] * g2[0] - g1[0] * g2[2];
+  double m2 = g1[0] * g2[1] - g1[1] * g2[0];
+  return g0[0] * m0 + g0[1] * m1 + g0[2] * m2;
+}
+
+// Error-free transformations on float (Dekker / Knuth): a*b = p + e and
+// a + b = s + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Determinant of float columns carried in float-float (about 44 significant
+// bits) and rounded once: each product of two entries is exact as a float
+// pair, each 2x2 minor and the final sum are compensated.  This keeps the
+// determinant at better than FP32 accuracy on the FP32 pipes; GB300's FP64
+// rate is 1/62 of its FP32 rate, so an FP64 determinant would bound the
+// mixed-precision stage.
+__device__ __forceinline__ float det3(const float g0[3], const float g1[3],
+                                      const float g2[3]) {
+  float th[3], tl[3];
+  const float* A = g1;
+  const float* B = g2;
+  const int ia[3] = {1, 2, 0}, ib[3] = {2, 0, 1};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float p, pe, q, qe, s, se;
+    two_prod(A[ia[r]], B[ib[r]], p, pe);
+    two_prod(A[ib[r]], B[ia[r]], q, qe);
+    two_sum(p, -q, s, se);
+    float lo = se + (pe - qe);
+    float t, te;
+    two_prod(g0[r], s, t, te);
+    te = fmaf(g0[r], lo, te);
+    th[r] = t;
+    tl[r] = te;
+  }
+  float s01, e01, s, e2;
+  two_sum(th[0], th[1], s01, e01);
+  two_sum(s01, th[2], s, e2);
+  float lo = ((tl[0] + tl[1]) + tl[2]) + (e01 + e2);
+  return s + lo;
+}
+
+template <typename C>
+__device__ __forceinline__ C dot3(const C a[3], const C b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+template <typename C>
+__device__ __forceinline__ C coef_a(const DevState* st, int s, int j);
+template <>
+__device__ __forceinline__ double coef_a<double>(const DevState* st, int s, int j) {
+  return st->dta[s][j];
+}
+template <>
+__device__ __forceinline__ float coef_a<float>(const DevState* st, int s, int j) {
+  return st->dtaf[s][j];
+}
+template <typename C>
+__device__ __forceinline__ C coef_b(const DevState* st, int j);
+template <>
+__device__ __forceinline__ double coef_b<double>(const DevState* st, int j) {
+  return st->dtb[j];
+}
+template <>
+__device__ __forceinline__ float coef_b<float>(const DevState* st, int j) {
+  return st->dtbf[j];
+}
+template <typename C>
+__device__ __forceinline__ C coef_e(const DevState* st, int j);
+template <>
+__device__ __forceinline__ double coef_e<double>(const DevState* st, int j) {
+  return st->dte[j];
+}
+template <>
+__device__ __forceinline__ float coef_e<float>(const DevState* st, int j) {
+  return st->dtef[j];
+}
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Deterministic block reduction (fixed tree); result valid in thread 0.
+template <bool MAX>
+__device__ __forceinline__ double block_reduce(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = MAX ? warp_max(v) : warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    v = MAX ? warp_max(v) : warp_sum(v);
+  }
+  return v;
+}
+
+// ------------------------------------------------------------ x_s planes
+
+// Form plane q of the stage input d_s = d + sum_{j<s} dt a_sj k_j over the
+// tile + halo `halo` into shared-memory slot `dst` (3 components of `pitch`
+// points each).  Planes outside the grid are skipped.
+template <typename T, typename C, int W, int H, int HALO>
+__device__ __forceinline__ void load_plane(const StageArgs<T>& a, const T* __restrict__ d,
+                                           const C* ca, int q, int i0, int j0,
+                                           C* __restrict__ dst) {
+  if (q < 0 || q >= a.nz) return;
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  for (int p = threadIdx.x; p < W * H; p += NT) {
+    const int lx = p % W, ly = p / W;
+    const int gi = i0 - HALO + lx, gj = j0 - HALO + ly;
+    if (gi < 0 || gi >= a.nx || gj < 0 || gj >= a.ny) continue;
+    const long long n = nidx(gi, gj, q, a.nx, a.ny);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      C v = (C)__ldg(&d[c * N + n]);
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if (j < a.stage) v = fma(ca[j], (C)__ldg(&a.k[j][c * N + n]), v);
+      dst[c * W * H + p] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ mimetic
+
+// B (and 1/det G) at every node of plane q in the tile + halo 1.  Index-space
+// differences: central inside, second-order one-sided on boundary faces.
+template <typename T, typename C>
+__device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, int j0,
+                                          int k0, int k1, const C* __restrict__ xs,
+                                          C* __restrict__ bs, bool diag, double& eacc) {
+  if (q < 0 || q >= a.nz) return;
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  const C* xq = xs + (q & 3) * 3 * XP;
+  const C* xm = xs + ((q - 1) & 3) * 3 * XP;
+  const C* xp = xs + ((q + 1) & 3) * 3 * XP;
+  const C* xm2 = xs + ((q - 2) & 3) * 3 * XP;
+  const C* xp2 = xs + ((q + 2) & 3) * 3 * XP;
+  C* bq = bs + (q % 3) * 4 * BP;
+  const C h20 = (C)a.h2[0], h21 = (C)a.h2[1], h22 = (C)a.h2[2];
+  for (int p = threadIdx.x; p < BP; p += NT) {
+    const int bx = p % BW, by = p / BW;
+    const int gi = i0 - 1 + bx, gj = j0 - 1 + by;
+    if (gi < 0 || gi >= a.nx || gj < 0 || gj >= a.ny) continue;
+    const int x0 = (by + 1) * XW + (bx + 1);
+    C g[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C* s = xq + c * XP;
+      if (gi > 0 && gi < a.nx - 1)
+        g[0][c] = s[x0 + 1] - s[x0 - 1];
+      else if (gi == 0)
+        g[0][c] = ((C)4 * s[x0 + 1] - (C)3 * s[x0]) - s[x0 + 2];
+      else
+        g[0][c] = ((C)3 * s[x0] - (C)4 * s[x0 - 1]) + s[x0 - 2];
+      if (gj > 0 && gj < a.ny - 1)
+        g[1][c] = s[x0 + XW] - s[x0 - XW];
+      else if (gj == 0)
+        g[1][c] = ((C)4 * s[x0 + XW] - (C)3 * s[x0]) - s[x0 + 2 * XW];
+      else
+        g[1][c] = ((C)3 * s[x0] - (C)4 * s[x0 - XW]) + s[x0 - 2 * XW];
+      if (q > 0 && q < a.nz - 1)
+        g[2][c] = xp[c * XP + x0] - xm[c * XP + x0];
+      else if (q == 0)
+        g[2][c] = ((C)4 * xp[c * XP + x0] - (C)3 * s[x0]) - xp2[c * XP + x0];
+      else
+        g[2][c] = ((C)3 * s[x0] - (C)4 * xm[c * XP + x0]) + xm2[c * XP + x0];
+    }
+    g[0][0] += h20;
+    g[1][1] += h21;
+    g[2][2] += h22;
+    const C det = det3(g[0], g[1], g[2]);
+    if (det <= (C)0)  // NaN: reported by the error norm
+    atomicOr(&a.st->flags, a.stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+    const C r = (C)1 / det;
+    const long long n = nidx(gi, gj, q, a.nx, a.ny);
+    const C b0 = (C)__ldg(&a.B0s[n]), b1 = (C)__ldg(&a.B0s[N + n]),
+            b2 = (C)__ldg(&a.B0s[2 * N + n]);
+    C B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      B[c] = (g[0][c] * b0 + g[1][c] * b1 + g[2][c] * b2) * r;
+      bq[c * BP + p] = B[c];
+    }
+    bq[3 * BP + p] = r;
+    if (diag && q >= k0 && q < k1 && bx >= 1 && bx <= TX && by >= 1 && by <= TY) {
+      // eq. "magnetic energy": zeta halves per boundary index coordinate
+      double zeta = 1.0;
+      if (gi == 0 || gi == a.nx - 1) zeta *= 0.5;
+      if (gj == 0 || gj == a.ny - 1) zeta *= 0.5;
+      if (q == 0 || q == a.nz - 1) zeta *= 0.5;
+      eacc += zeta * (double)dot3(B, B) * (double)det;
+    }
+  }
+}
+
+// Per-CTA accumulators of the diagnostic and error reductions.
+struct Acc {
+  double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
+};
+
+// Stage output at a node: write k_s, or (last stage) the update and error.
+template <typename T, typename C, bool FINAL>
+__device__ __forceinline__ void emit(const StageArgs<T>& a, long long n, const C u[3],
+                                     const C J[3], const C B[3], const T* __restrict__ d,
+                                     T* __restrict__ dout, const DevState* st, bool diag,
+                                     Acc& acc) {
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  if (diag) {
+    const double u2 = (double)dot3(u, u), b2 = (double)dot3(B, B),
+                 j2 = (double)dot3(J, J);
+    // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
+    if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
+    const double jb = j2 * b2;
+    if (jb > 1e-300 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+  }
+  if (!FINAL) {
+    T* ko = a.k[a.stage];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ko[c * N + n] = (T)u[c];
+  } else {
+    // fifth-order update (b_2 = b_5 = 0) and embedded error (b_2 - b*_2 = 0)
+    const C b0 = coef_b<C>(st, 0), b2 = coef_b<C>(st, 2), b3 = coef_b<C>(st, 3),
+            b5 = coef_b<C>(st, 5);
+    const C e0 = coef_e<C>(st, 0), e2 = coef_e<C>(st, 2), e3 = coef_e<C>(st, 3),
+            e4 = coef_e<C>(st, 4), e5 = coef_e<C>(st, 5);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C k1 = (C)__ldg(&a.k[0][c * N + n]), k3 = (C)__ldg(&a.k[2][c * N + n]),
+              k4 = (C)__ldg(&a.k[3][c * N + n]), k5 = (C)__ldg(&a.k[4][c * N + n]);
+      C up = b0 * k1;
+      up = fma(b2, k3, up);
+      up = fma(b3, k4, up);
+      up = fma(b5, u[c], up);
+      C er = e0 * k1;
+      er = fma(e2, k3, er);
+      er = fma(e3, k4, er);
+      er = fma(e4, k5, er);
+      er = fma(e5, u[c], er);
+      dout[c * N + n] = (T)((C)__ldg(&d[c * N + n]) + up);
+      acc.lam = nanmax(acc.lam, (double)fabs(er));
+    }
+  }
+}
+
+// Mimetic current and velocity at the tile's nodes of plane m.
+template <typename T, typename C, bool FINAL>
+__device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int i0, int j0,
+                                            const C* __restrict__ xs,
+                                            const C* __restrict__ bs, const T* d, T* dout,
+                                            const DevState* st, bool diag, Acc& acc) {
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gi = i0 + tx, gj = j0 + ty;
+  if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
+  const int x0 = (ty + 2) * XW + (tx + 2);
+  const int b0i = (ty + 1) * BW + (tx + 1);
+  const C* xq = xs + (m & 3) * 3 * XP;
+  const C* xm = xs + ((m - 1) & 3) * 3 * XP;
+  const C* xp = xs + ((m + 1) & 3) * 3 * XP;
+  const C* bq = bs + (m % 3) * 4 * BP;
+  const C* bm = bs + ((m + 2) % 3) * 4 * BP;
+  const C* bp = bs + ((m + 1) % 3) * 4 * BP;
+  C g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C* s = xq + c * XP;
+    g0[c] = s[x0 + 1] - s[x0 - 1];
+    g1[c] = s[x0 + XW] - s[x0 - XW];
+    g2[c] = xp[c * XP + x0] - xm[c * XP + x0];
+    const C* b = bq + c * BP;
+    P0[c] = b[b0i + 1] - b[b0i - 1];
+    P1[c] = b[b0i + BW] - b[b0i - BW];
+    P2[c] = bp[c * BP + b0i] - bm[c * BP + b0i];
+    B[c] = b[b0i];
+  }
+  g0[0] += (C)a.h2[0];
+  g1[1] += (C)a.h2[1];
+  g2[2] += (C)a.h2[2];
+  const C c0 = dot3(P1, g2) - dot3(P2, g1);
+  const C c1 = dot3(P2, g0) - dot3(P0, g2);
+  const C c2 = dot3(P0, g1) - dot3(P1, g0);
+  const C r = bq[3 * BP + b0i];
+  C J[3], u[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
+  u[0] = J[1] * B[2] - J[2] * B[1];
+  u[1] = J[2] * B[0] - J[0] * B[2];
+  u[2] = J[0] * B[1] - J[1] * B[0];
+  emit<T, C, FINAL>(a, nidx(gi, gj, m, a.nx, a.ny), u, J, B, d, dout, st, diag, acc);
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void write_partials(const StageArgs<T>& a, bool final_stage,
+                                               bool diag, Acc& acc, double* red) {
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (final_stage) {
+    const double v = block_reduce<true>(acc.lam, red);
+    if (threadIdx.x == 0) a.part[PART_LAMBDA * a.nblocks + bid] = v;
+  }
+  if (diag) {
+    double v = block_reduce<false>(acc.e, red);
+    if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
+    v = block_reduce<true>(acc.xi2, red);
+    if (threadIdx.x == 0) a.part[PART_XI2 * a.nblocks + bid] = v;
+    v = block_reduce<true>(acc.xis2, red);
+    if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
+  }
+}
+
+template <typename T, typename C, bool FINAL, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a) {
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  C* xs = reinterpret_cast<C*>(smem_raw);  // [4 planes][3][XP]
+  C* bs = xs + 4 * 3 * XP;                 // [3 planes][B0,B1,B2,1/det][BP]
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
+  const int cur = st->cur;
+  const T* d = a.d[cur];
+  T* dout = const_cast<T*>(a.d[cur ^ 1]);
+  C ca[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) ca[j] = j < a.stage ? coef_a<C>(st, a.stage, j) : (C)0;
+  const bool diag = a.diag != 0;
+  Acc acc;
+  // prologue: planes k0-2 .. k0+1, then B(k0-1), plane k0+2, B(k0)
+  for (int q = k0 - 2; q <= k0 + 1; ++q)
+    load_plane<T, C, XW, XH, 2>(a, d, ca, q, i0, j0, xs + (q & 3) * 3 * XP);
+  __syncthreads();
+  compute_B<T, C>(a, k0 - 1, i0, j0, k0, k1, xs, bs, diag, acc.e);
+  __syncthreads();
+  load_plane<T, C, XW, XH, 2>(a, d, ca, k0 + 2, i0, j0, xs + ((k0 + 2) & 3) * 3 * XP);
+  __syncthreads();
+  compute_B<T, C>(a, k0, i0, j0, k0, k1, xs, bs, diag, acc.e);
+  __syncthreads();
+  for (int m = k0; m < k1; ++m) {
+    compute_B<T, C>(a, m + 1, i0, j0, k0, k1, xs, bs, diag, acc.e);
+    __syncthreads();
+    mimetic_out<T, C, FINAL>(a, m, i0, j0, xs, bs, d, dout, st, diag, acc);
+    __syncthreads();
+    load_plane<T, C, XW, XH, 2>(a, d, ca, m + 3, i0, j0, xs + ((m + 3) & 3) * 3 * XP);
+    __syncthreads();
+  }
+  write_partials<T, C>(a, FINAL, diag, acc, red);
+}
+
+// ------------------------------------------------------------ direct
+
+template <typename T, typename C, bool FINAL>
+__device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0, int j0,
+                                           const C* __restrict__ xs, const T* d, T* dout,
+                                           const DevState* st, bool diag, Acc& acc) {
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gi = i0 + tx, gj = j0 + ty;
+  if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  const int p0 = (ty + 1) * DW + (tx + 1);
+  const C* xq = xs + (m % 3) * 3 * DP;
+  const C* xm = xs + ((m + 2) % 3) * 3 * DP;
+  const C* xp = xs + ((m + 1) % 3) * 3 * DP;
+  // columns g_a of G and the second differences S_ac = S_ca (index space)
+  C g[3][3], S[3][3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C* s = xq + c * DP;
+    const C* sm = xm + c * DP;
+    const C* sp = xp + c * DP;
+    const C xc = s[p0];
+    g[0][c] = s[p0 + 1] - s[p0 - 1];
+    g[1][c] = s[p0 + DW] - s[p0 - DW];
+    g[2][c] = sp[p0] - sm[p0];
+    S[0][0][c] = (C)4 * ((s[p0 + 1] + s[p0 - 1]) - (C)2 * xc);
+    S[1][1][c] = (C)4 * ((s[p0 + DW] + s[p0 - DW]) - (C)2 * xc);
+    S[2][2][c] = (C)4 * ((sp[p0] + sm[p0]) - (C)2 * xc);
+    S[0][1][c] = (s[p0 + 1 + DW] - s[p0 + 1 - DW]) - (s[p0 - 1 + DW] - s[p0 - 1 - DW]);
+    S[0][2][c] = (sp[p0 + 1] - sm[p0 + 1]) - (sp[p0 - 1] - sm[p0 - 1]);
+    S[1][2][c] = (sp[p0 + DW] - sm[p0 + DW]) - (sp[p0 - DW] - sm[p0 - DW]);
+    S[1][0][c] = S[0][1][c];
+    S[2][0][c] = S[0][2][c];
+    S[2][1][c] = S[1][2][c];
+  }
+  g[0][0] += (C)a.h2[0];
+  g[1][1] += (C)a.h2[1];
+  g[2][2] += (C)a.h2[2];
+  // B0s at the node and its differences D_c B0s = B0s(+e_c) - B0s(-e_c)
+  const long long n = nidx(gi, gj, m, a.nx, a.ny);
+  const long long sx = 1, sy = a.nx, sz = (long long)a.nx * a.ny;
+  C b[3], Db[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* B0 = a.B0s + c * N;
+    b[c] = (C)__ldg(&B0[n]);
+    Db[0][c] = (C)__ldg(&B0[n + sx]) - (C)__ldg(&B0[n - sx]);
+    Db[1][c] = (C)__ldg(&B0[n + sy]) - (C)__ldg(&B0[n - sy]);
+    Db[2][c] = (C)__ldg(&B0[n + sz]) - (C)__ldg(&B0[n - sz]);
+  }
+  // cofactors of G: row i of cof is (row i+1 of G) x (row i+2 of G)
+  C cof[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    cof[i][0] = g[1][i1] * g[2][i2] - g[2][i1] * g[1][i2];
+    cof[i][1] = g[2][i1] * g[0][i2] - g[0][i1] * g[2][i2];
+    cof[i][2] = g[0][i1] * g[1][i2] - g[1][i1] * g[0][i2];
+  }
+  const C det = det3(g[0], g[1], g[2]);
+  if (det <= (C)0)  // NaN: reported by the error norm
+    atomicOr(&a.st->flags, a.stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+  const C r = (C)1 / det;
+  C V[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) V[i] = g[0][i] * b[0] + g[1][i] * b[1] + g[2][i] * b[2];
+  // D_c B = D_c V / det - V D_c det / det^2, with
+  // D_c V = sum_a S_ac b_a + g_a D_c b_a and D_c det = sum_ia cof_ia (S_ac)_i
+  C DB[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C Dd = (C)0;
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Dd = fma(cof[i][aa], S[aa][c][i], Dd);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      C DV = (C)0;
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) DV = fma(S[aa][c][i], b[aa], fma(g[aa][i], Db[c][aa], DV));
+      DB[c][i] = (DV - V[i] * Dd * r) * r;
+    }
+  }
+  // grad B (gB[i][l] = dB_i/dx_l) = sum_c D_c B_i (G^-1)_cl, G^-1 = cof^T / det
+  C gB[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      gB[i][l] = (DB[0][i] * cof[l][0] + DB[1][i] * cof[l][1] + DB[2][i] * cof[l][2]) * r;
+  C J[3], B[3], u[3];
+  J[0] = gB[2][1] - gB[1][2];
+  J[1] = gB[0][2] - gB[2][0];
+  J[2] = gB[1][0] - gB[0][1];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) B[i] = V[i] * r;
+  u[0] = J[1] * B[2] - J[2] * B[1];
+  u[1] = J[2] * B[0] - J[0] * B[2];
+  u[2] = J[0] * B[1] - J[1] * B[0];
+  emit<T, C, FINAL>(a, n, u, J, B, d, dout, st, diag, acc);
+}
+
+template <typename T, typename C, bool FINAL, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a) {
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  C* xs = reinterpret_cast<C*>(smem_raw);  // [3 planes][3][DP]
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
+  const int cur = st->cur;
+  const T* d = a.d[cur];
+  T* dout = const_cast<T*>(a.d[cur ^ 1]);
+  C ca[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) ca[j] = j < a.stage ? coef_a<C>(st, a.stage, j) : (C)0;
+  const bool diag = a.diag != 0;
+  Acc acc;
+  for (int q = k0 - 1; q <= k0; ++q)
+    if (q >= 0) load_plane<T, C, DW, DH, 1>(a, d, ca, q, i0, j0, xs + (q % 3) * 3 * DP);
+  for (int m = k0; m < k1; ++m) {
+    load_plane<T, C, DW, DH, 1>(a, d, ca, m + 1, i0, j0, xs + ((m + 1) % 3) * 3 * DP);
+    __syncthreads();
+    direct_out<T, C, FINAL>(a, m, i0, j0, xs, d, dout, st, diag, acc);
+    __syncthreads();
+  }
+  write_partials<T, C>(a, FINAL, diag, acc, red);
+}
+
+// ------------------------------------------------------------ launchers
+
+inline size_t stage_smem_bytes(int curl, size_t csize) {
+  return curl == 0 ? (size_t)(4 * 3 * XP + 3 * 4 * BP) * csize
+                   : (size_t)(3 * 3 * DP) * csize;
+}
+
+}  // namespace glemur

@@ -1,0 +1,258 @@
+"""Thin Python binding of the C ABI in include/glemur.h (argument marshalling
+only; every step of the relaxation runs in the CUDA library).
+
+Fields are float64 arrays of shape (3, nz, ny, nx): a CUDA torch tensor is
+passed as a device pointer, a numpy array (or CPU tensor) as a host pointer.
+PyTorch supplies the device workspace and the stream; the library allocates
+nothing.  There is no CPU fallback: without the compiled library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR = {-1: "BADARG", -2: "CUDA", -3: "COLLAPSED", -4: "NONFINITE", -5: "DT_UNDERFLOW",
+       -6: "WORKSPACE"}
+FP64, MIXED = 0, 1
+MIMETIC, DIRECT = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class GlemurError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {ERR.get(code, code)} ({code})")
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("curl", C.c_int), ("lambda0", C.c_double),
+                ("dt0", C.c_double), ("dt_min", C.c_double), ("grow_max", C.c_double),
+                ("shrink_min", C.c_double), ("max_rejects", C.c_int),
+                ("diag_each_attempt", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("t", C.c_double),
+                ("dt", C.c_double), ("lambda_", C.c_double), ("energy", C.c_double),
+                ("xi", C.c_double), ("xi_sin", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return dict(accepted=self.accepted, rejected=self.rejected, t=self.t, dt=self.dt,
+                    lam=self.lambda_, energy=self.energy, xi=self.xi, xi_sin=self.xi_sin,
+                    status=self.status)
+
+
+EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
+           "glemur_set_x", "glemur_set_B0", "glemur_get_x", "glemur_velocity",
+           "glemur_step", "glemur_attempts", "glemur_step_fixed", "glemur_energy",
+           "glemur_forcefree_err", "glemur_get_stats", "glemur_kernels_per_attempt",
+           "glemur_profile_attempt", "glemur_destroy", "glemur_strerror"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> C.CDLL:
+    """Load libglemur.so (building it first when the toolkit is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    try:
+        path = _build.build()
+    except Exception as e:  # no toolkit: use an existing build or fail loudly
+        if not os.path.exists(path):
+            raise RuntimeError(f"libglemur.so is not built and cannot be built: {e}") from e
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    L.glemur_default_opts.argtypes = [C.POINTER(Opts)]
+    L.glemur_default_opts.restype = None
+    L.glemur_workspace_bytes.argtypes = [ip, ip, ip, ip]
+    L.glemur_workspace_bytes.restype = C.c_size_t
+    L.glemur_init_grid.argtypes = [C.POINTER(vp), ip, ip, ip, dp, dp, C.POINTER(Opts), vp, vp,
+                                   C.c_size_t]
+    L.glemur_set_x.argtypes = [vp, vp, ip]
+    L.glemur_set_B0.argtypes = [vp, vp, ip]
+    L.glemur_get_x.argtypes = [vp, vp, ip]
+    L.glemur_velocity.argtypes = [vp, vp, ip]
+    L.glemur_step.argtypes = [vp, ip, C.POINTER(Stats)]
+    L.glemur_attempts.argtypes = [vp, ip]
+    L.glemur_step_fixed.argtypes = [vp, C.c_double, C.POINTER(Stats)]
+    L.glemur_energy.argtypes = [vp, dp]
+    L.glemur_forcefree_err.argtypes = [vp, dp, dp]
+    L.glemur_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.glemur_kernels_per_attempt.argtypes = [vp]
+    L.glemur_profile_attempt.argtypes = [vp, C.POINTER(C.c_float), ip]
+    L.glemur_destroy.argtypes = [vp]
+    L.glemur_destroy.restype = None
+    L.glemur_strerror.argtypes = [ip]
+    L.glemur_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise GlemurError(rc, what)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().glemur_default_opts(C.byref(o))
+    return o
+
+
+def workspace_bytes(nx, ny, nz, precision=FP64) -> int:
+    return int(lib().glemur_workspace_bytes(nx, ny, nz, precision))
+
+
+def _field_ptr(a, shape, writable=False):
+    """(pointer, mem kind, keep-alive) of a float64 (3, nz, ny, nx) field."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if tuple(a.shape) != shape or a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError(f"expected contiguous float64 tensor of shape {shape}")
+            return (a.data_ptr(), MEM_DEVICE if a.is_cuda else MEM_HOST, a)
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.shape != shape or arr.dtype != np.float64 or not arr.flags.c_contiguous:
+        if writable:
+            raise ValueError(f"expected C-contiguous float64 array of shape {shape}")
+        arr = np.ascontiguousarray(arr, dtype=np.float64).reshape(shape)
+    return (arr.ctypes.data, MEM_HOST, arr)
+
+
+class Relaxation:
+    """A grid of nx*ny*nz nodes with labels on [lo, hi] and its relaxation
+    state, bound to one CUDA device and stream (glemur_init_grid)."""
+
+    def __init__(self, nx, ny, nz, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                 precision=FP64, curl=MIMETIC, lambda0=None, dt0=None, dt_min=None,
+                 grow_max=None, shrink_min=None, max_rejects=None, diag_each_attempt=None,
+                 device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the GB300 relaxation library needs a CUDA device")
+        self.shape = (3, nz, ny, nx)
+        self.dims = (nx, ny, nz)
+        self.device = torch.device(device if device is not None else "cuda")
+        o = default_opts()
+        o.precision, o.curl = int(precision), int(curl)
+        for name, v in (("lambda0", lambda0), ("dt0", dt0), ("dt_min", dt_min),
+                        ("grow_max", grow_max), ("shrink_min", shrink_min),
+                        ("max_rejects", max_rejects), ("diag_each_attempt", diag_each_attempt)):
+            if v is not None:
+                setattr(o, name, type(getattr(o, name))(v))
+        self.opts = o
+        L = lib()
+        nbytes = L.glemur_workspace_bytes(nx, ny, nz, o.precision)
+        if nbytes == 0:
+            raise GlemurError(-1, "glemur_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+            lo_a = (C.c_double * 3)(*lo)
+            hi_a = (C.c_double * 3)(*hi)
+            h = C.c_void_p()
+            rc = L.glemur_init_grid(C.byref(h), nx, ny, nz, lo_a, hi_a, C.byref(o),
+                                    C.c_void_p(self.stream.cuda_stream),
+                                    C.c_void_p(self.workspace.data_ptr()), int(nbytes))
+        _check(rc, "glemur_init_grid")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.glemur_destroy(h)
+            self._h = None
+
+    # -- fields -----------------------------------------------------------
+    def set_x(self, x):
+        p, mem, keep = _field_ptr(x, self.shape)
+        _check(lib().glemur_set_x(self._h, p, mem), "glemur_set_x")
+        self._sync_if(mem)
+
+    def set_B0(self, B0):
+        p, mem, keep = _field_ptr(B0, self.shape)
+        _check(lib().glemur_set_B0(self._h, p, mem), "glemur_set_B0")
+        self._sync_if(mem)
+
+    def _sync_if(self, mem):
+        if mem == MEM_HOST:  # the host buffer may be released on return
+            self.stream.synchronize()
+
+    def get_x(self, out=None):
+        """Current positions: into `out` (CUDA tensor or numpy array), else a
+        new CUDA tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        p, mem, keep = _field_ptr(out, self.shape, writable=True)
+        _check(lib().glemur_get_x(self._h, p, mem), "glemur_get_x")
+        return out
+
+    def velocity(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        p, mem, keep = _field_ptr(out, self.shape, writable=True)
+        _check(lib().glemur_velocity(self._h, p, mem), "glemur_velocity")
+        return out
+
+    # -- stepping ---------------------------------------------------------
+    def step(self, n_accept=1, check=True):
+        st = Stats()
+        rc = lib().glemur_step(self._h, int(n_accept), C.byref(st))
+        if check:
+            _check(rc, "glemur_step")
+        return st.as_dict()
+
+    def attempts(self, n):
+        _check(lib().glemur_attempts(self._h, int(n)), "glemur_attempts")
+
+    def step_fixed(self, dt, check=True):
+        st = Stats()
+        rc = lib().glemur_step_fixed(self._h, float(dt), C.byref(st))
+        if check:
+            _check(rc, "glemur_step_fixed")
+        return st.as_dict()
+
+    def stats(self):
+        st = Stats()
+        _check(lib().glemur_get_stats(self._h, C.byref(st)), "glemur_get_stats")
+        return st.as_dict()
+
+    # -- diagnostics ------------------------------------------------------
+    def energy(self):
+        e = C.c_double()
+        _check(lib().glemur_energy(self._h, C.byref(e)), "glemur_energy")
+        return e.value
+
+    def forcefree_err(self):
+        a, b = C.c_double(), C.c_double()
+        _check(lib().glemur_forcefree_err(self._h, C.byref(a), C.byref(b)),
+               "glemur_forcefree_err")
+        return a.value, b.value
+
+    def kernels_per_attempt(self):
+        return int(lib().glemur_kernels_per_attempt(self._h))
+
+    def profile_attempt(self):
+        """One attempt with per-kernel CUDA-event durations (ms), launch order:
+        stages 1..6, step control."""
+        ms = (C.c_float * 16)()
+        n = lib().glemur_profile_attempt(self._h, ms, 16)
+        if n < 0:
+            raise GlemurError(n, "glemur_profile_attempt")
+        return [ms[i] for i in range(n)]

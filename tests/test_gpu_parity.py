@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Tolerances.  FP64: both sides evaluate the same quantities with O(100)
+double operations, in different order; element-wise agreement is required to
+1e-11 of the field's max-norm for velocities (a difference quotient of B over
+2h amplifies B's rounding by ~1/h) and, as the method's target states, to
+1e-12 relative per step and 1e-10 after 100 steps in x.  Mixed precision:
+FP32 storage and stencils carry ~6e-8 relative rounding into differences
+over 2h (~1/h amplification, h ~ 1/30) and a second difference for J, so the
+velocity is held to 2e-4 of its max-norm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import glemur_inputs as gi
+import oracle as ora
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1405_0942_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def braid_case(nx, ny, nz, seed=2, regions=None):
+    g = gi.Grid(nx, ny, nz)
+    X = gi.nodes(g)
+    regs = regions or gi.braid_regions(6, None, True)
+    return g, gi.predistort(X, seed), gi.braid_field(X, regs)
+
+
+def relaxation(G, g, x0, B0, precision=0, curl=0, **kw):
+    r = G.Relaxation(g.nx, g.ny, g.nz, g.lo, g.hi, precision=precision, curl=curl, **kw)
+    r.set_x(torch.from_numpy(np.ascontiguousarray(x0)).cuda())
+    r.set_B0(torch.from_numpy(np.ascontiguousarray(B0)).cuda())
+    return r
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SIZES = [(3, 3, 3), (16, 16, 16), (37, 19, 23), (33, 9, 70)]
+
+
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+@pytest.mark.parametrize("dims", SIZES, ids=lambda d: "x".join(map(str, d)))
+def test_velocity_fp64(G, dims, curl):
+    g, x0, B0 = braid_case(*dims)
+    r = relaxation(G, g, x0, B0, curl=curl)
+    u = r.velocity().cpu().numpy()
+    u_ref, rc = ora.velocity(g, x0, B0, curl)
+    assert rc == ora.OK
+    assert rel_inf(u, u_ref) < 1e-11
+    # line-tied boundary: exactly zero
+    ub = u.copy()
+    ub[:, 1:-1, 1:-1, 1:-1] = 0
+    assert np.all(ub == 0)
+
+
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+@pytest.mark.parametrize("dims", [(16, 16, 16), (37, 19, 23)], ids=lambda d: "x".join(map(str, d)))
+def test_velocity_mixed(G, dims, curl):
+    g, x0, B0 = braid_case(*dims)
+    r = relaxation(G, g, x0, B0, precision=1, curl=curl)
+    u = r.velocity().cpu().numpy()
+    u_ref, _ = ora.velocity(g, x0, B0, curl)
+    assert rel_inf(u, u_ref) < 2e-4
+
+
+def test_positions_round_trip(G):
+    g, x0, B0 = braid_case(20, 11, 9)
+    for prec, tol in ((0, 0.0), (1, 1e-8)):
+        r = relaxation(G, g, x0, B0, precision=prec)
+        x = r.get_x().cpu().numpy()
+        assert np.abs(x - x0).max() <= tol
+        xh = np.empty_like(x0)
+        r.get_x(out=xh)
+        assert np.array_equal(xh, x)
+
+
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+def test_one_step_fp64(G, curl):
+    """One Cash-Karp step of fixed size: x within 1e-12 relative."""
+    g, x0, B0 = braid_case(24, 20, 28)
+    dt = 2e-3
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, curl)
+    r = relaxation(G, g, x0, B0, curl=curl)
+    st = r.step_fixed(dt)
+    x = r.get_x().cpu().numpy()
+    assert st["accepted"] == 1
+    assert rel_inf(x, x_ref) < 1e-12
+    # the displacement of the step itself agrees far below its size
+    assert np.abs(x - x_ref).max() < 1e-9 * np.abs(x_ref - x0).max()
+    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref
+
+
+def test_hundred_steps_replayed_schedule_fp64(G):
+    """100 error-controlled steps of the oracle; the GPU replays the accepted
+    step sizes: x within 1e-10 relative."""
+    w = gi.make_workload("tube", n=16)
+    g = w.grid
+    x_ref, dt_next, log, st_ref, rc = ora.relax(g, w.x0, w.B0, 100, 1e-3)
+    assert rc == ora.OK and len(log) == 100
+    r = relaxation(G, g, w.x0, w.B0)
+    for dt in log:
+        r.step_fixed(dt)
+    x = r.get_x().cpu().numpy()
+    assert rel_inf(x, x_ref) < 1e-10
+
+
+def test_error_control_matches_oracle(G):
+    """Free-running control: same accept/reject sequence and step sizes."""
+    g, x0, B0 = braid_case(14, 14, 14)
+    opts = ora.ControlOpts(lambda0=1e-8)
+    r = relaxation(G, g, x0, B0, lambda0=1e-8, dt0=5e-2)
+    x_ref, dt_ref, log, st_ref, rc = ora.relax(g, x0, B0, 20, 5e-2, opts=opts)
+    assert rc == ora.OK
+    st = r.step(20)
+    assert st_ref["rejected"] > 0           # the control law is exercised
+    assert st["accepted"] == 20 and st["rejected"] == st_ref["rejected"]
+    assert abs(st["dt"] - dt_ref) < 1e-12 * dt_ref
+    assert abs(st["t"] - st_ref["t"]) < 1e-12 * st_ref["t"]
+    assert rel_inf(r.get_x().cpu().numpy(), x_ref) < 1e-11
+
+
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+def test_diagnostics_fp64(G, curl):
+    g, x0, B0 = braid_case(29, 17, 21)
+    r = relaxation(G, g, x0, B0, curl=curl)
+    E_ref, _ = ora.energy(g, x0, B0)
+    xi_ref, xis_ref, _ = ora.forcefree(g, x0, B0, curl)
+    assert abs(r.energy() - E_ref) < 1e-13 * E_ref
+    xi, xis = r.forcefree_err()
+    assert abs(xi - xi_ref) < 1e-10 * xi_ref
+    assert abs(xis - xis_ref) < 1e-10 * xis_ref
+    # the per-attempt reduction reports the state the attempt starts from
+    st = r.step(1)
+    if curl == 0:
+        assert abs(st["energy"] - E_ref) < 1e-13 * E_ref
+    else:
+        assert math.isnan(st["energy"])
+    assert abs(st["xi"] - xi_ref) < 1e-10 * xi_ref
+
+
+def test_diagnostics_mixed(G):
+    g, x0, B0 = braid_case(29, 17, 21)
+    r = relaxation(G, g, x0, B0, precision=1)
+    E_ref, _ = ora.energy(g, x0, B0)
+    xi_ref, xis_ref, _ = ora.forcefree(g, x0, B0)
+    assert abs(r.energy() - E_ref) < 1e-6 * E_ref
+    xi, xis = r.forcefree_err()
+    assert abs(xi - xi_ref) < 1e-3 * xi_ref
+
+
+def test_energy_decays_on_gpu(G):
+    w = gi.make_workload("tube", n=16)
+    r = relaxation(G, w.grid, w.x0, w.B0)
+    E = [r.energy()]
+    for _ in range(10):
+        r.step(20)
+        E.append(r.energy())
+    assert np.all(np.diff(E) <= 1e-13 * E[0]) and E[-1] < E[0]
+
+
+# ------------------------------------------------------------------ edges
+
+
+def test_single_interior_node(G):
+    g = gi.Grid(3, 3, 3)
+    X = gi.nodes(g)
+    x0 = X + 0.01 * np.sin(3 * X[[1, 2, 0]])
+    x0[:, [0, -1], :, :] = X[:, [0, -1], :, :]
+    B0 = gi.braid_field(X, [(0.1, 0.0, 0.0, 1.0, 0.7, 0.7)])
+    r = relaxation(G, g, x0, B0)
+    u_ref, _ = ora.velocity(g, x0, B0)
+    assert rel_inf(r.velocity().cpu().numpy(), u_ref) < 1e-11
+
+
+def test_uniform_field_is_stationary(G):
+    g = gi.Grid(12, 10, 9)
+    X = gi.nodes(g)
+    A = np.array([[1.1, 0.2, 0.0], [-0.1, 0.9, 0.3], [0.05, 0.0, 1.2]])
+    x0 = np.einsum("ab,b...->a...", A, X)
+    B0 = gi.uniform_field(g, (0.3, -0.2, 1.0))
+    r = relaxation(G, g, x0, B0)
+    assert np.abs(r.velocity().cpu().numpy()).max() < 1e-12
+    st = r.step(3)
+    assert st["rejected"] == 0 and abs(st["dt"] - 0.125) < 1e-15
+    assert np.abs(r.get_x().cpu().numpy() - x0).max() < 1e-13
+
+
+def test_zero_steps_is_a_noop(G):
+    g, x0, B0 = braid_case(8, 8, 8)
+    r = relaxation(G, g, x0, B0)
+    st = r.step(0)
+    assert st["accepted"] == 0 and st["rejected"] == 0
+    assert np.array_equal(r.get_x().cpu().numpy(), x0)
+
+
+def test_collapsed_grid_is_reported(G):
+    g = gi.Grid(6, 6, 6)
+    X = gi.nodes(g)
+    x0 = X.copy()
+    x0[0, 2, 2, 2] = X[0, 2, 2, 4] + 0.3
+    r = relaxation(G, g, x0, gi.uniform_field(g))
+    st = r.step(1, check=False)
+    assert st["status"] == -3
+    with pytest.raises(G.GlemurError):
+        r.step(1)
+    r.set_x(torch.from_numpy(X.copy()).cuda())     # set_x clears the error
+    assert r.step(1)["status"] == 0
+
+
+def test_nonfinite_field_is_reported(G):
+    g, x0, B0 = braid_case(8, 8, 8)
+    B0 = B0.copy()
+    B0[1, 4, 4, 4] = np.nan
+    r = relaxation(G, g, x0, B0)
+    assert r.step(1, check=False)["status"] == -4
+
+
+def test_step_underflow_is_reported(G):
+    g, x0, B0 = braid_case(10, 10, 10)
+    r = relaxation(G, g, x0, B0, lambda0=1e-300, max_rejects=5)
+    st = r.step(1, check=False)
+    assert st["status"] == -5 and st["accepted"] == 0 and st["rejected"] == 6
+
+
+def test_host_buffers_round_trip(G):
+    """GLEMUR_MEM_HOST paths: host x/B0 in, host x/u out."""
+    g, x0, B0 = braid_case(17, 13, 11)
+    r = G.Relaxation(g.nx, g.ny, g.nz)
+    r.set_x(x0)
+    r.set_B0(B0)
+    u = np.empty_like(x0)
+    r.velocity(out=u)
+    u_ref, _ = ora.velocity(g, x0, B0)
+    assert rel_inf(u, u_ref) < 1e-11
+
+
+# --------------------------------------------- full-size, sampled outputs
+
+
+def _sample_nodes(g, count, seed):
+    rng = np.random.default_rng(seed)
+    pts = [(1, 1, 1), (g.nx - 2, g.ny - 2, g.nz - 2), (1, g.ny - 2, g.nz // 2),
+           (g.nx // 2, 1, g.nz - 2)]
+    for _ in range(count):
+        pts.append(tuple(int(rng.integers(1, n - 1)) for n in (g.nx, g.ny, g.nz)))
+    return pts
+
+
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+def test_full_size_braid64_sampled(G, curl):
+    """The 64^3 braid workload in the benchmark's launch configuration: the
+    stage-1 velocity at sampled nodes against the oracle one node at a time."""
+    w = gi.make_workload("braid")
+    g = w.grid
+    r = relaxation(G, g, w.x0, w.B0, curl=curl)
+    u = r.velocity().cpu().numpy()
+    scale = np.abs(u).max()
+    for (i, j, k) in _sample_nodes(g, 60, 1):
+        un, rc = ora.velocity_at(g, w.x0, w.B0, i, j, k, curl)
+        assert rc == ora.OK
+        assert np.abs(u[:, k, j, i] - un).max() < 1e-11 * scale, (i, j, k)
+
+
+def test_full_size_prod384_sampled_mixed(G):
+    """The 384^3 production workload (mixed precision): sampled velocities
+    against the FP64 oracle within the mixed-precision tolerance."""
+    w = gi.make_workload("prod")
+    g = w.grid
+    r = relaxation(G, g, w.x0, w.B0, precision=1)
+    u = r.velocity()
+    scale = float(u.abs().max())
+    for (i, j, k) in _sample_nodes(g, 40, 2):
+        un, rc = ora.velocity_at(g, w.x0, w.B0, i, j, k)
+        assert np.abs(u[:, k, j, i].cpu().numpy() - un).max() < 2e-4 * scale, (i, j, k)
+    del r
+    torch.cuda.empty_cache()

@@ -523,3 +523,21 @@ def test_velocity_at_matches_field():
         for (i, j, k) in [(1, 1, 1), (5, 7, 3), (10, 10, 10), (0, 4, 4)]:
             un, rc = ora.velocity_at(w.grid, w.x0, w.B0, i, j, k, curl)
             assert np.array_equal(un, u[:, k, j, i])
+
+
+def test_folded_trial_stage_rejects_the_attempt():
+    """A step size far beyond stability folds a trial stage input: the
+    attempt is rejected with the largest shrink (dt x 0.1), not fatal, and
+    the run continues (section "Grid Convexity and Stability": the step
+    collapses before a blow-up)."""
+    g = gi.Grid(12, 12, 12)
+    X = gi.nodes(g)
+    B0 = gi.braid_field(X, [(0.0, 0.0, 0.0, 3.0, 0.4, 0.4)])
+    u, _ = ora.velocity(g, X, B0)
+    dt_big = 5.0                                   # far beyond the stable step
+    xs = X + 0.2 * dt_big * u                      # the Cash-Karp stage-2 input
+    _, _, rc = ora.pullback(g, xs, B0)
+    assert rc == ora.ERR_COLLAPSED                 # a trial stage is folded
+    x, dt, log, st, rc = ora.relax(g, X, B0, 3, dt_big, opts=ora.ControlOpts(lambda0=1e-6))
+    assert rc == ora.OK and st["accepted"] == 3 and st["rejected"] >= 1
+    assert log[0] <= 0.1 * dt_big * (1 + 1e-12)
