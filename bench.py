@@ -281,7 +281,7 @@ def our_arm(args):
     per_kernel = ms.mean(axis=0).tolist()
 
     extra = {}
-    if rank == 0 and ws == 1 and not args.no_compare:
+    if rank == 0 and ws == 1 and not (args.no_compare or args.lean):
         for prec, curl in (("mixed", "mimetic"), ("fp64", "direct"), ("mixed", "direct")):
             if (prec, curl) == (args.precision, args.curl):
                 continue
@@ -291,12 +291,13 @@ def our_arm(args):
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.sum(axis=1).mean(),
                 "speedup_vs_primary": v2 / value,
                 "roofline": roofline_entry(ms2, w, prec, curl, hbm_peak, peak_kind)}
-    e2e = e2e_measure(G, torch, w, args.precision, args.curl, max(3, min(args.steps, 10)))
+    e2e = None if args.lean else e2e_measure(G, torch, w, args.precision, args.curl,
+                                             max(3, min(args.steps, 10)))
     if ws > 1:
         torch.distributed.barrier()
     if rank != 0:
         return
-    cb = run_oracle_sample(w, 12.0, 1000, args.curl) if ws == 1 else None
+    cb = run_oracle_sample(w, 12.0, 1000, args.curl) if ws == 1 and not args.lean else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms.sum(axis=1).mean(),
@@ -322,6 +323,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--curl", default="mimetic", choices=["mimetic", "direct"])
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--lean", action="store_true",
+                    help="timed steps only: no comparisons, e2e or CPU baseline (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

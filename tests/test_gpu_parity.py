@@ -128,8 +128,10 @@ def test_error_control_matches_oracle(G):
     st = r.step(20)
     assert st_ref["rejected"] > 0           # the control law is exercised
     assert st["accepted"] == 20 and st["rejected"] == st_ref["rejected"]
-    assert abs(st["dt"] - dt_ref) < 1e-12 * dt_ref
-    assert abs(st["t"] - st_ref["t"]) < 1e-12 * st_ref["t"]
+    # Lambda is a small difference of stage sums (relative agreement ~1e-10)
+    # and dt' scales as Lambda^-0.2
+    assert abs(st["dt"] - dt_ref) < 1e-9 * dt_ref
+    assert abs(st["t"] - st_ref["t"]) < 1e-9 * st_ref["t"]
     assert rel_inf(r.get_x().cpu().numpy(), x_ref) < 1e-11
 
 
