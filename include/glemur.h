@@ -67,7 +67,9 @@ enum glemur_status {
   GLEMUR_ERR_NONFINITE = -4,    /* NaN/Inf in the error estimate */
   GLEMUR_ERR_DT_UNDERFLOW = -5, /* step shrank below dt_min or too many
                                    consecutive rejections */
-  GLEMUR_ERR_WORKSPACE = -6     /* workspace missing, misaligned or small */
+  GLEMUR_ERR_WORKSPACE = -6,    /* workspace missing, misaligned or small */
+  GLEMUR_ERR_TOO_LARGE = -7     /* grid larger than a fixed-scratch entry
+                                   point supports */
 };
 
 typedef struct glemur_ctx glemur_ctx;
@@ -184,6 +186,30 @@ int glemur_kernels_per_attempt(const glemur_ctx* ctx);
  * the step control), n = glemur_kernels_per_attempt(ctx) <= cap.  Returns n,
  * or a negative error (BADARG if cap < n). */
 int glemur_profile_attempt(glemur_ctx* ctx, float* ms, int cap);
+
+/* Largest grid (nodes) glemur_energy_static accepts: 256^3. */
+#define GLEMUR_STATIC_MAX_NODES (1LL << 24)
+
+/* Magnetic energy E_M of positions x with initial field B0, allocating
+ * nothing: for callers that cannot allocate device memory (a host framework
+ * that owns the whole device pool and forbids foreign allocations, or code
+ * that must not trigger the implicit device synchronisation of
+ * cudaMalloc/cudaFree).  The paper has no counterpart; this is the energy
+ * reduction of glemur_energy without a context or workspace.
+ * x and B0 are device float64 fields (layout above) of an nx*ny*nz grid
+ * with labels on [lo, hi]; *E (device memory, one double) receives E_M,
+ * computed as glemur_energy does (FP64, fixed-order sums).  The per-CTA
+ * partial sums live in a static device array of GLEMUR_STATIC_MAX_NODES/256
+ * doubles (512 KiB) that every GPU loading this library holds until the
+ * process exits; grids of more than GLEMUR_STATIC_MAX_NODES nodes return
+ * GLEMUR_ERR_TOO_LARGE.  The first call on each device resolves that
+ * array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (different streams or threads) race.  Asynchronous on `stream` (a
+ * cudaStream_t or NULL).  Errors: BADARG, TOO_LARGE, CUDA. */
+int glemur_energy_static(int nx, int ny, int nz, const double lo[3],
+                         const double hi[3], const double* x, const double* B0,
+                         double* E, void* stream);
 
 /* Release the context (host memory only; the workspace stays the
  * caller's). NULL is ignored. */

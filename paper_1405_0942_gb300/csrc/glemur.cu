@@ -728,6 +728,7 @@ const char* glemur_strerror(int status) {
     case GLEMUR_ERR_NONFINITE: return "non-finite error estimate";
     case GLEMUR_ERR_DT_UNDERFLOW: return "step size underflow / too many rejections";
     case GLEMUR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case GLEMUR_ERR_TOO_LARGE: return "grid larger than the fixed scratch supports";
     default: return "unknown status";
   }
 }

@@ -18,7 +18,7 @@ from . import build as _build
 
 OK = 0
 ERR = {-1: "BADARG", -2: "CUDA", -3: "COLLAPSED", -4: "NONFINITE", -5: "DT_UNDERFLOW",
-       -6: "WORKSPACE"}
+       -6: "WORKSPACE", -7: "TOO_LARGE"}
 FP64, MIXED = 0, 1
 MIMETIC, DIRECT = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
@@ -52,7 +52,8 @@ EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
            "glemur_set_x", "glemur_set_B0", "glemur_get_x", "glemur_velocity",
            "glemur_step", "glemur_attempts", "glemur_step_fixed", "glemur_energy",
            "glemur_forcefree_err", "glemur_get_stats", "glemur_kernels_per_attempt",
-           "glemur_profile_attempt", "glemur_destroy", "glemur_strerror"]
+           "glemur_profile_attempt", "glemur_energy_static", "glemur_destroy",
+           "glemur_strerror"]
 
 _lib = None
 
@@ -92,6 +93,7 @@ def lib() -> C.CDLL:
     L.glemur_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.glemur_kernels_per_attempt.argtypes = [vp]
     L.glemur_profile_attempt.argtypes = [vp, C.POINTER(C.c_float), ip]
+    L.glemur_energy_static.argtypes = [ip, ip, ip, dp, dp, vp, vp, vp, vp]
     L.glemur_destroy.argtypes = [vp]
     L.glemur_destroy.restype = None
     L.glemur_strerror.argtypes = [ip]
