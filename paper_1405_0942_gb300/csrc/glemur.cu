@@ -13,14 +13,18 @@
 #include "glemur_dev.cuh"
 
 namespace glemur {
-cudaError_t prepare_stage_f64();
-cudaError_t prepare_stage_f32();
-int stage_ctas_per_sm_f64(int curl);
-int stage_ctas_per_sm_f32(int curl);
-cudaError_t launch_stage_f64(const StageArgs<double>& a, int curl, bool final_stage,
-                             dim3 grid, cudaStream_t s);
-cudaError_t launch_stage_f32(const StageArgs<float>& a, int curl, bool final_stage,
-                             dim3 grid, cudaStream_t s);
+cudaError_t launch_f64_mimetic(const StageArgs<double>& a, int stage, dim3 grid, cudaStream_t s);
+cudaError_t launch_f64_direct(const StageArgs<double>& a, int stage, dim3 grid, cudaStream_t s);
+cudaError_t launch_f32_mimetic(const StageArgs<float>& a, int stage, dim3 grid, cudaStream_t s);
+cudaError_t launch_f32_direct(const StageArgs<float>& a, int stage, dim3 grid, cudaStream_t s);
+cudaError_t prepare_f64_mimetic();
+cudaError_t prepare_f64_direct();
+cudaError_t prepare_f32_mimetic();
+cudaError_t prepare_f32_direct();
+int ctas_per_sm_f64_mimetic();
+int ctas_per_sm_f64_direct();
+int ctas_per_sm_f32_mimetic();
+int ctas_per_sm_f32_direct();
 
 // Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
 // of section "Time Stepping".
@@ -281,8 +285,9 @@ struct glemur_ctx {
   double* stage;    // 3N doubles for host transfers
   double* part;     // NPART * max_blocks
   DevState* st;
-  int max_blocks, nblocks, kz;
-  dim3 grid;
+  int max_blocks, nblocks, kz;          // mimetic-current launches
+  int nblocks_direct, kz_direct;         // direct-current launches
+  dim3 grid, grid_direct;
   int nsm;
 };
 
@@ -295,8 +300,9 @@ struct Layout {
   int max_blocks;
 };
 
+// Kernels index the three components of a field with 32-bit ints.
 bool valid_dims(int nx, int ny, int nz) {
-  return nx >= 3 && ny >= 3 && nz >= 3 && (long long)nx * ny * nz <= (1LL << 40);
+  return nx >= 3 && ny >= 3 && nz >= 3 && 3LL * nx * ny * nz < (1LL << 31);
 }
 
 Layout layout(int nx, int ny, int nz, int precision) {
@@ -333,16 +339,22 @@ int elementwise_blocks(long long n) {
   return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
 }
 
-// Planes per CTA: minimise (waves) x (planes + 2 halo planes) per CTA.
-int choose_kz(int nz, int gxy, int cap) {
+// Planes per CTA along z.  Cost model: the time of the busiest SM, in units
+// of one B plane (a CTA of kz planes computes kz + 2 B planes).  FP64 stages
+// are bound by the SM's FP64 pipe, which co-resident CTAs share, so an SM's
+// time is its CTA count x (kz + 2); the FP32 stages are latency-bound, so
+// up to `per_sm` co-resident CTAs overlap and the time is waves x (kz + 2).
+int choose_kz(int nz, int gxy, int nsm, int per_sm, bool shared_pipe) {
   const char* env = getenv("GLEMUR_KZ");
   if (env && atoi(env) > 0) return atoi(env) < nz ? atoi(env) : nz;
-  if (cap < 1) cap = 1;
+  if (nsm < 1) nsm = 1;
+  if (per_sm < 1) per_sm = 1;
   int best = nz;
   double best_cost = 1e300;
   for (int kz = 1; kz <= nz; ++kz) {
     const long long ctas = (long long)gxy * ((nz + kz - 1) / kz);
-    const double waves = (double)((ctas + cap - 1) / cap);
+    const long long slots = shared_pipe ? nsm : (long long)nsm * per_sm;
+    const double waves = (double)((ctas + slots - 1) / slots);
     const double cost = waves * (kz + 2);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
@@ -359,7 +371,10 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.ny = c->ny;
   a.nz = c->nz;
   a.kz = c->kz;
-  for (int i = 0; i < 3; ++i) a.h2[i] = 2.0 * c->h[i];
+  for (int i = 0; i < 3; ++i) {
+    a.h2[i] = 2.0 * c->h[i];
+    a.h2f[i] = (float)a.h2[i];
+  }
   a.d[0] = (const T*)c->dbuf[0];
   a.d[1] = (const T*)c->dbuf[1];
   a.B0s = (const T*)c->B0s;
@@ -373,11 +388,28 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   return a;
 }
 
+int nblocks_of(const glemur_ctx* c, int curl) {
+  return curl == GLEMUR_CURL_DIRECT ? c->nblocks_direct : c->nblocks;
+}
+
 cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force) {
-  const bool fin = stage == 5;
-  if (c->o.precision == GLEMUR_MIXED)
-    return launch_stage_f32(make_args<float>(c, stage, diag, force), curl, fin, c->grid, c->s);
-  return launch_stage_f64(make_args<double>(c, stage, diag, force), curl, fin, c->grid, c->s);
+  const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
+  if (c->o.precision == GLEMUR_MIXED) {
+    StageArgs<float> a = make_args<float>(c, stage, diag, force);
+    if (curl == GLEMUR_CURL_DIRECT) {
+      a.kz = c->kz_direct;
+      a.nblocks = c->nblocks_direct;
+      return launch_f32_direct(a, stage, g, c->s);
+    }
+    return launch_f32_mimetic(a, stage, g, c->s);
+  }
+  StageArgs<double> a = make_args<double>(c, stage, diag, force);
+  if (curl == GLEMUR_CURL_DIRECT) {
+    a.kz = c->kz_direct;
+    a.nblocks = c->nblocks_direct;
+    return launch_f64_direct(a, stage, g, c->s);
+  }
+  return launch_f64_mimetic(a, stage, g, c->s);
 }
 
 cudaError_t launch_attempt(const glemur_ctx* c) {
@@ -386,7 +418,7 @@ cudaError_t launch_attempt(const glemur_ctx* c) {
     cudaError_t e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
     if (e != cudaSuccess) return e;
   }
-  k_control<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks, diag);
+  k_control<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, c->o.curl), diag);
   return cudaGetLastError();
 }
 
@@ -512,17 +544,22 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = o.precision == GLEMUR_MIXED ? prepare_stage_f32() : prepare_stage_f64();
+  const bool mixed = o.precision == GLEMUR_MIXED;
+  if (e == cudaSuccess) e = mixed ? prepare_f32_mimetic() : prepare_f64_mimetic();
+  if (e == cudaSuccess) e = mixed ? prepare_f32_direct() : prepare_f64_direct();
   if (e != cudaSuccess) {
     delete c;
     return GLEMUR_ERR_CUDA;
   }
-  const int per_sm = o.precision == GLEMUR_MIXED ? stage_ctas_per_sm_f32(o.curl)
-                                                  : stage_ctas_per_sm_f64(o.curl);
   const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
-  c->kz = choose_kz(nz, gx * gy, per_sm * c->nsm);
+  const int pm = mixed ? ctas_per_sm_f32_mimetic() : ctas_per_sm_f64_mimetic();
+  const int pd = mixed ? ctas_per_sm_f32_direct() : ctas_per_sm_f64_direct();
+  c->kz = choose_kz(nz, gx * gy, c->nsm, pm, !mixed);
   c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
   c->nblocks = gx * gy * (int)c->grid.z;
+  c->kz_direct = choose_kz(nz, gx * gy, c->nsm, pd, !mixed);
+  c->grid_direct = dim3(gx, gy, (nz + c->kz_direct - 1) / c->kz_direct);
+  c->nblocks_direct = gx * gy * (int)c->grid_direct.z;
 
   // zero displacement (x = X), B0 and stage fields; boundary entries of the
   // stage fields stay zero for ever (line-tied nodes do not move)
@@ -649,7 +686,7 @@ int glemur_energy(glemur_ctx* c, double* E) {
   if (!c || !E) return GLEMUR_ERR_BADARG;
   cudaError_t e = launch_stage(c, GLEMUR_CURL_MIMETIC, 0, 1, 1);
   if (e == cudaSuccess) {
-    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks);
+    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, GLEMUR_CURL_MIMETIC));
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
@@ -664,7 +701,7 @@ int glemur_forcefree_err(glemur_ctx* c, double* xi, double* xi_sin) {
   if (!c || !xi || !xi_sin) return GLEMUR_ERR_BADARG;
   cudaError_t e = launch_stage(c, c->o.curl, 0, 1, 1);
   if (e == cudaSuccess) {
-    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks);
+    k_diag_finalize<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, c->o.curl));
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
@@ -707,7 +744,7 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
   if (e == cudaSuccess) {
-    k_control<<<1, 256, 0, c->s>>>(c->st, c->part, c->nblocks, diag);
+    k_control<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, c->o.curl), diag);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->s);

@@ -74,6 +74,7 @@ struct StageArgs {
   int nx, ny, nz;
   int kz;              // planes per CTA along z
   double h2[3];        // 2 h_a
+  float h2f[3];        // 2 h_a rounded to float (mixed precision)
   const T* d[2];       // ping-pong displacement buffers (3N each)
   const T* B0s;        // pre-scaled B0 (3N)
   T* k[5];             // stage derivatives k1..k5 (3N each)

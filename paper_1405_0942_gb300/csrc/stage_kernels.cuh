@@ -22,6 +22,13 @@
 // with c_r the right-hand sides: the same J as the paper's loop form, with
 // no 3x3 solve and det G the one the pull-back already needs.
 //
+// Pipeline (mimetic kernel).  Shared memory holds a ring of 6 planes of x_s
+// and a ring of 4 planes of B.  Iteration m computes B at plane m+2, the
+// current at plane m and the stage input of plane m+4: the three touch
+// disjoint ring slots, so one barrier per plane suffices, and the global
+// loads of plane m+4 are issued before, and committed after, the arithmetic
+// of the other two.
+//
 // Direct current (the classic method).  dB/dX follows from B = G B0s / det G
 // by the product rule with second differences of x, differences of B0s and
 // Jacobi's formula for d det G; dB/dx = dB/dX G^-1 (index-space scaling
@@ -64,14 +71,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ float det3(const float g0[3], const float g1[3],
                                       const float g2[3]) {
   float th[3], tl[3];
-  const float* A = g1;
-  const float* B = g2;
   const int ia[3] = {1, 2, 0}, ib[3] = {2, 0, 1};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     float p, pe, q, qe, s, se;
-    two_prod(A[ia[r]], B[ib[r]], p, pe);
-    two_prod(A[ib[r]], B[ia[r]], q, qe);
+    two_prod(g1[ia[r]], g2[ib[r]], p, pe);
+    two_prod(g1[ib[r]], g2[ia[r]], q, qe);
     two_sum(p, -q, s, se);
     float lo = se + (pe - qe);
     float t, te;
@@ -123,6 +128,17 @@ __device__ __forceinline__ float coef_e<float>(const DevState* st, int j) {
   return st->dtef[j];
 }
 
+template <typename T, typename C>
+__device__ __forceinline__ C h2of(const StageArgs<T>& a, int i);
+template <>
+__device__ __forceinline__ double h2of<double, double>(const StageArgs<double>& a, int i) {
+  return a.h2[i];
+}
+template <>
+__device__ __forceinline__ float h2of<float, float>(const StageArgs<float>& a, int i) {
+  return a.h2f[i];
+}
+
 // ------------------------------------------------------------ reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -151,50 +167,97 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   return v;
 }
 
+// Per-CTA accumulators of the diagnostic and error reductions.
+struct Acc {
+  double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
+};
+
 // ------------------------------------------------------------ x_s planes
 
-// Form plane q of the stage input d_s = d + sum_{j<s} dt a_sj k_j over the
-// tile + halo `halo` into shared-memory slot `dst` (3 components of `pitch`
-// points each).  Planes outside the grid are skipped.
-template <typename T, typename C, int W, int H, int HALO>
-__device__ __forceinline__ void load_plane(const StageArgs<T>& a, const T* __restrict__ d,
-                                           const C* ca, int q, int i0, int j0,
-                                           C* __restrict__ dst) {
-  if (q < 0 || q >= a.nz) return;
-  const long long N = (long long)a.nx * a.ny * a.nz;
-  for (int p = threadIdx.x; p < W * H; p += NT) {
-    const int lx = p % W, ly = p / W;
-    const int gi = i0 - HALO + lx, gj = j0 - HALO + ly;
-    if (gi < 0 || gi >= a.nx || gj < 0 || gj >= a.ny) continue;
-    const long long n = nidx(gi, gj, q, a.nx, a.ny);
+// The shared-memory points of a W x H tile (+halo) that this thread loads:
+// LP slots, each the in-plane offset gj*nx + gi of the node, or -1.
+template <int W, int H, int HALO>
+struct LoadPts {
+  static constexpr int LP = (W * H + NT - 1) / NT;
+  int off[LP];
+  __device__ __forceinline__ void init(int i0, int j0, int nx, int ny) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      C v = (C)__ldg(&d[c * N + n]);
-#pragma unroll
-      for (int j = 0; j < 5; ++j)
-        if (j < a.stage) v = fma(ca[j], (C)__ldg(&a.k[j][c * N + n]), v);
-      dst[c * W * H + p] = v;
+    for (int t = 0; t < LP; ++t) {
+      const int p = threadIdx.x + t * NT;
+      off[t] = -1;
+      if (p < W * H) {
+        const int gi = i0 - HALO + p % W, gj = j0 - HALO + p / W;
+        if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) off[t] = gj * nx + gi;
+      }
     }
   }
-}
+};
+
+// Global values of plane q needed for its stage input (d and k_1..k_S at the
+// thread's points), held in registers between issue and commit.
+template <typename T, typename C, int S, int LP>
+struct PlaneRaw {
+  C v[LP][3][S + 1];
+
+  __device__ __forceinline__ void issue(const StageArgs<T>& a, const T* __restrict__ d,
+                                        const int* off, int q) {
+    const int N = a.nx * a.ny * a.nz;
+    const int base = q * a.nx * a.ny;
+#pragma unroll
+    for (int t = 0; t < LP; ++t) {
+      if (off[t] < 0) continue;
+      const int n = base + off[t];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[t][c][0] = (C)__ldg(&d[c * N + n]);
+#pragma unroll
+        for (int j = 0; j < S; ++j) v[t][c][j + 1] = (C)__ldg(&a.k[j][c * N + n]);
+      }
+    }
+  }
+
+  // d_s = d + sum_j (dt a_sj) k_j into the shared-memory plane `dst`.
+  template <int PITCH>
+  __device__ __forceinline__ void commit(const C* ca, const int* off, C* __restrict__ dst) const {
+#pragma unroll
+    for (int t = 0; t < LP; ++t) {
+      if (off[t] < 0) continue;
+      const int p = threadIdx.x + t * NT;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C s = v[t][c][0];
+#pragma unroll
+        for (int j = 0; j < S; ++j) s = fma(ca[j], v[t][c][j + 1], s);
+        dst[c * PITCH + p] = s;
+      }
+    }
+  }
+};
 
 // ------------------------------------------------------------ mimetic
+
+constexpr int XRING = 6;  // planes of x_s in shared memory
+constexpr int BRING = 4;  // planes of B (+ 1/det G) in shared memory
+
+__device__ __forceinline__ int xslot(int q) { return (q + XRING) % XRING; }
+__device__ __forceinline__ int bslot(int q) { return (q + BRING) % BRING; }
 
 // B (and 1/det G) at every node of plane q in the tile + halo 1.  Index-space
 // differences: central inside, second-order one-sided on boundary faces.
 template <typename T, typename C>
 __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, int j0,
                                           int k0, int k1, const C* __restrict__ xs,
-                                          C* __restrict__ bs, bool diag, double& eacc) {
-  if (q < 0 || q >= a.nz) return;
-  const long long N = (long long)a.nx * a.ny * a.nz;
-  const C* xq = xs + (q & 3) * 3 * XP;
-  const C* xm = xs + ((q - 1) & 3) * 3 * XP;
-  const C* xp = xs + ((q + 1) & 3) * 3 * XP;
-  const C* xm2 = xs + ((q - 2) & 3) * 3 * XP;
-  const C* xp2 = xs + ((q + 2) & 3) * 3 * XP;
-  C* bq = bs + (q % 3) * 4 * BP;
-  const C h20 = (C)a.h2[0], h21 = (C)a.h2[1], h22 = (C)a.h2[2];
+                                          C* __restrict__ bs, bool diag, bool state,
+                                          double& eacc) {
+  const int N = a.nx * a.ny * a.nz;
+  const C* xq = xs + xslot(q) * 3 * XP;
+  const C* xm = xs + xslot(q - 1) * 3 * XP;
+  const C* xp = xs + xslot(q + 1) * 3 * XP;
+  const C* xm2 = xs + xslot(q - 2) * 3 * XP;
+  const C* xp2 = xs + xslot(q + 2) * 3 * XP;
+  C* bq = bs + bslot(q) * 4 * BP;
+  const C h20 = h2of<T, C>(a, 0), h21 = h2of<T, C>(a, 1), h22 = h2of<T, C>(a, 2);
+  const bool zlo = q == 0, zhi = q == a.nz - 1;
   for (int p = threadIdx.x; p < BP; p += NT) {
     const int bx = p % BW, by = p / BW;
     const int gi = i0 - 1 + bx, gj = j0 - 1 + by;
@@ -216,9 +279,9 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
         g[1][c] = ((C)4 * s[x0 + XW] - (C)3 * s[x0]) - s[x0 + 2 * XW];
       else
         g[1][c] = ((C)3 * s[x0] - (C)4 * s[x0 - XW]) + s[x0 - 2 * XW];
-      if (q > 0 && q < a.nz - 1)
+      if (!zlo && !zhi)
         g[2][c] = xp[c * XP + x0] - xm[c * XP + x0];
-      else if (q == 0)
+      else if (zlo)
         g[2][c] = ((C)4 * xp[c * XP + x0] - (C)3 * s[x0]) - xp2[c * XP + x0];
       else
         g[2][c] = ((C)3 * s[x0] - (C)4 * xm[c * XP + x0]) + xm2[c * XP + x0];
@@ -228,9 +291,9 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
     g[2][2] += h22;
     const C det = det3(g[0], g[1], g[2]);
     if (det <= (C)0)  // NaN: reported by the error norm
-    atomicOr(&a.st->flags, a.stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+      atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
     const C r = (C)1 / det;
-    const long long n = nidx(gi, gj, q, a.nx, a.ny);
+    const int n = (q * a.ny + gj) * a.nx + gi;
     const C b0 = (C)__ldg(&a.B0s[n]), b1 = (C)__ldg(&a.B0s[N + n]),
             b2 = (C)__ldg(&a.B0s[2 * N + n]);
     C B[3];
@@ -245,24 +308,19 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
       double zeta = 1.0;
       if (gi == 0 || gi == a.nx - 1) zeta *= 0.5;
       if (gj == 0 || gj == a.ny - 1) zeta *= 0.5;
-      if (q == 0 || q == a.nz - 1) zeta *= 0.5;
+      if (zlo || zhi) zeta *= 0.5;
       eacc += zeta * (double)dot3(B, B) * (double)det;
     }
   }
 }
 
-// Per-CTA accumulators of the diagnostic and error reductions.
-struct Acc {
-  double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
-};
-
 // Stage output at a node: write k_s, or (last stage) the update and error.
 template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void emit(const StageArgs<T>& a, long long n, const C u[3],
+__device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, const C u[3],
                                      const C J[3], const C B[3], const T* __restrict__ d,
                                      T* __restrict__ dout, const DevState* st, bool diag,
                                      Acc& acc) {
-  const long long N = (long long)a.nx * a.ny * a.nz;
+  const int N = a.nx * a.ny * a.nz;
   if (diag) {
     const double u2 = (double)dot3(u, u), b2 = (double)dot3(B, B),
                  j2 = (double)dot3(J, J);
@@ -272,7 +330,7 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, long long n, const C
     if (jb > 1e-300 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
   }
   if (!FINAL) {
-    T* ko = a.k[a.stage];
+    T* ko = a.k[stage];
 #pragma unroll
     for (int c = 0; c < 3; ++c) ko[c * N + n] = (T)u[c];
   } else {
@@ -302,8 +360,8 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, long long n, const C
 
 // Mimetic current and velocity at the tile's nodes of plane m.
 template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int i0, int j0,
-                                            const C* __restrict__ xs,
+__device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, int m, int i0,
+                                            int j0, const C* __restrict__ xs,
                                             const C* __restrict__ bs, const T* d, T* dout,
                                             const DevState* st, bool diag, Acc& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -311,12 +369,12 @@ __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int i0
   if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
   const int x0 = (ty + 2) * XW + (tx + 2);
   const int b0i = (ty + 1) * BW + (tx + 1);
-  const C* xq = xs + (m & 3) * 3 * XP;
-  const C* xm = xs + ((m - 1) & 3) * 3 * XP;
-  const C* xp = xs + ((m + 1) & 3) * 3 * XP;
-  const C* bq = bs + (m % 3) * 4 * BP;
-  const C* bm = bs + ((m + 2) % 3) * 4 * BP;
-  const C* bp = bs + ((m + 1) % 3) * 4 * BP;
+  const C* xq = xs + xslot(m) * 3 * XP;
+  const C* xm = xs + xslot(m - 1) * 3 * XP;
+  const C* xp = xs + xslot(m + 1) * 3 * XP;
+  const C* bq = bs + bslot(m) * 4 * BP;
+  const C* bm = bs + bslot(m - 1) * 4 * BP;
+  const C* bp = bs + bslot(m + 1) * 4 * BP;
   C g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -330,9 +388,9 @@ __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int i0
     P2[c] = bp[c * BP + b0i] - bm[c * BP + b0i];
     B[c] = b[b0i];
   }
-  g0[0] += (C)a.h2[0];
-  g1[1] += (C)a.h2[1];
-  g2[2] += (C)a.h2[2];
+  g0[0] += h2of<T, C>(a, 0);
+  g1[1] += h2of<T, C>(a, 1);
+  g2[2] += h2of<T, C>(a, 2);
   const C c0 = dot3(P1, g2) - dot3(P2, g1);
   const C c1 = dot3(P2, g0) - dot3(P0, g2);
   const C c2 = dot3(P0, g1) - dot3(P1, g0);
@@ -343,7 +401,7 @@ __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int i0
   u[0] = J[1] * B[2] - J[2] * B[1];
   u[1] = J[2] * B[0] - J[0] * B[2];
   u[2] = J[0] * B[1] - J[1] * B[0];
-  emit<T, C, FINAL>(a, nidx(gi, gj, m, a.nx, a.ny), u, J, B, d, dout, st, diag, acc);
+  emit<T, C, FINAL>(a, stage, (m * a.ny + gj) * a.nx + gi, u, J, B, d, dout, st, diag, acc);
 }
 
 template <typename T, typename C>
@@ -364,40 +422,51 @@ __device__ __forceinline__ void write_partials(const StageArgs<T>& a, bool final
   }
 }
 
-template <typename T, typename C, bool FINAL, int MINB>
+// Stage S (0..5) of Cash-Karp with the mimetic current.
+template <typename T, typename C, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a) {
+  constexpr bool FINAL = S == 5;
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
-  C* xs = reinterpret_cast<C*>(smem_raw);  // [4 planes][3][XP]
-  C* bs = xs + 4 * 3 * XP;                 // [3 planes][B0,B1,B2,1/det][BP]
+  C* xs = reinterpret_cast<C*>(smem_raw);  // [XRING][3][XP]
+  C* bs = xs + XRING * 3 * XP;             // [BRING][B0,B1,B2,1/det][BP]
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
   const int cur = st->cur;
   const T* d = a.d[cur];
   T* dout = const_cast<T*>(a.d[cur ^ 1]);
-  C ca[5];
+  C ca[S > 0 ? S : 1];
 #pragma unroll
-  for (int j = 0; j < 5; ++j) ca[j] = j < a.stage ? coef_a<C>(st, a.stage, j) : (C)0;
+  for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
   const bool diag = a.diag != 0;
   Acc acc;
-  // prologue: planes k0-2 .. k0+1, then B(k0-1), plane k0+2, B(k0)
-  for (int q = k0 - 2; q <= k0 + 1; ++q)
-    load_plane<T, C, XW, XH, 2>(a, d, ca, q, i0, j0, xs + (q & 3) * 3 * XP);
+  LoadPts<XW, XH, 2> pts;
+  pts.init(i0, j0, a.nx, a.ny);
+  using Raw = PlaneRaw<T, C, S, LoadPts<XW, XH, 2>::LP>;
+  // prologue: stage input planes k0-2 .. k0+3, then B at k0-1 .. k0+1
+  for (int q = k0 - 2; q <= k0 + 3; ++q) {
+    if (q < 0 || q >= a.nz || q > k1 + 1) continue;
+    Raw raw;
+    raw.issue(a, d, pts.off, q);
+    raw.template commit<XP>(ca, pts.off, xs + xslot(q) * 3 * XP);
+  }
   __syncthreads();
-  compute_B<T, C>(a, k0 - 1, i0, j0, k0, k1, xs, bs, diag, acc.e);
-  __syncthreads();
-  load_plane<T, C, XW, XH, 2>(a, d, ca, k0 + 2, i0, j0, xs + ((k0 + 2) & 3) * 3 * XP);
-  __syncthreads();
-  compute_B<T, C>(a, k0, i0, j0, k0, k1, xs, bs, diag, acc.e);
+  for (int q = k0 - 1; q <= k0 + 1; ++q)
+    if (q >= 0 && q < a.nz && q <= k1)
+      compute_B<T, C>(a, q, i0, j0, k0, k1, xs, bs, diag, S == 0, acc.e);
   __syncthreads();
   for (int m = k0; m < k1; ++m) {
-    compute_B<T, C>(a, m + 1, i0, j0, k0, k1, xs, bs, diag, acc.e);
-    __syncthreads();
-    mimetic_out<T, C, FINAL>(a, m, i0, j0, xs, bs, d, dout, st, diag, acc);
-    __syncthreads();
-    load_plane<T, C, XW, XH, 2>(a, d, ca, m + 3, i0, j0, xs + ((m + 3) & 3) * 3 * XP);
+    const int qn = m + 4;  // stage input plane loaded in this iteration
+    const bool load = qn < a.nz && qn <= k1 + 1;
+    Raw raw;
+    if (load) raw.issue(a, d, pts.off, qn);
+    const int qb = m + 2;  // B plane computed in this iteration
+    if (qb < a.nz && qb <= k1)
+      compute_B<T, C>(a, qb, i0, j0, k0, k1, xs, bs, diag, S == 0, acc.e);
+    mimetic_out<T, C, FINAL>(a, S, m, i0, j0, xs, bs, d, dout, st, diag, acc);
+    if (load) raw.template commit<XP>(ca, pts.off, xs + xslot(qn) * 3 * XP);
     __syncthreads();
   }
   write_partials<T, C>(a, FINAL, diag, acc, red);
@@ -406,19 +475,19 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
 // ------------------------------------------------------------ direct
 
 template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0, int j0,
-                                           const C* __restrict__ xs, const T* d, T* dout,
-                                           const DevState* st, bool diag, Acc& acc) {
+__device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int m, int i0,
+                                           int j0, const C* __restrict__ xs, const T* d,
+                                           T* dout, const DevState* st, bool diag, Acc& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gi = i0 + tx, gj = j0 + ty;
   if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
-  const long long N = (long long)a.nx * a.ny * a.nz;
+  const int N = a.nx * a.ny * a.nz;
   const int p0 = (ty + 1) * DW + (tx + 1);
   const C* xq = xs + (m % 3) * 3 * DP;
   const C* xm = xs + ((m + 2) % 3) * 3 * DP;
   const C* xp = xs + ((m + 1) % 3) * 3 * DP;
   // columns g_a of G and the second differences S_ac = S_ca (index space)
-  C g[3][3], S[3][3][3];
+  C g[3][3], Sd[3][3][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const C* s = xq + c * DP;
@@ -428,22 +497,22 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0,
     g[0][c] = s[p0 + 1] - s[p0 - 1];
     g[1][c] = s[p0 + DW] - s[p0 - DW];
     g[2][c] = sp[p0] - sm[p0];
-    S[0][0][c] = (C)4 * ((s[p0 + 1] + s[p0 - 1]) - (C)2 * xc);
-    S[1][1][c] = (C)4 * ((s[p0 + DW] + s[p0 - DW]) - (C)2 * xc);
-    S[2][2][c] = (C)4 * ((sp[p0] + sm[p0]) - (C)2 * xc);
-    S[0][1][c] = (s[p0 + 1 + DW] - s[p0 + 1 - DW]) - (s[p0 - 1 + DW] - s[p0 - 1 - DW]);
-    S[0][2][c] = (sp[p0 + 1] - sm[p0 + 1]) - (sp[p0 - 1] - sm[p0 - 1]);
-    S[1][2][c] = (sp[p0 + DW] - sm[p0 + DW]) - (sp[p0 - DW] - sm[p0 - DW]);
-    S[1][0][c] = S[0][1][c];
-    S[2][0][c] = S[0][2][c];
-    S[2][1][c] = S[1][2][c];
+    Sd[0][0][c] = (C)4 * ((s[p0 + 1] + s[p0 - 1]) - (C)2 * xc);
+    Sd[1][1][c] = (C)4 * ((s[p0 + DW] + s[p0 - DW]) - (C)2 * xc);
+    Sd[2][2][c] = (C)4 * ((sp[p0] + sm[p0]) - (C)2 * xc);
+    Sd[0][1][c] = (s[p0 + 1 + DW] - s[p0 + 1 - DW]) - (s[p0 - 1 + DW] - s[p0 - 1 - DW]);
+    Sd[0][2][c] = (sp[p0 + 1] - sm[p0 + 1]) - (sp[p0 - 1] - sm[p0 - 1]);
+    Sd[1][2][c] = (sp[p0 + DW] - sm[p0 + DW]) - (sp[p0 - DW] - sm[p0 - DW]);
+    Sd[1][0][c] = Sd[0][1][c];
+    Sd[2][0][c] = Sd[0][2][c];
+    Sd[2][1][c] = Sd[1][2][c];
   }
-  g[0][0] += (C)a.h2[0];
-  g[1][1] += (C)a.h2[1];
-  g[2][2] += (C)a.h2[2];
+  g[0][0] += h2of<T, C>(a, 0);
+  g[1][1] += h2of<T, C>(a, 1);
+  g[2][2] += h2of<T, C>(a, 2);
   // B0s at the node and its differences D_c B0s = B0s(+e_c) - B0s(-e_c)
-  const long long n = nidx(gi, gj, m, a.nx, a.ny);
-  const long long sx = 1, sy = a.nx, sz = (long long)a.nx * a.ny;
+  const int n = (m * a.ny + gj) * a.nx + gi;
+  const int sx = 1, sy = a.nx, sz = a.nx * a.ny;
   C b[3], Db[3][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -464,7 +533,7 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0,
   }
   const C det = det3(g[0], g[1], g[2]);
   if (det <= (C)0)  // NaN: reported by the error norm
-    atomicOr(&a.st->flags, a.stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+    atomicOr(&a.st->flags, stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   const C r = (C)1 / det;
   C V[3];
 #pragma unroll
@@ -478,12 +547,12 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0,
 #pragma unroll
     for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Dd = fma(cof[i][aa], S[aa][c][i], Dd);
+      for (int i = 0; i < 3; ++i) Dd = fma(cof[i][aa], Sd[aa][c][i], Dd);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       C DV = (C)0;
 #pragma unroll
-      for (int aa = 0; aa < 3; ++aa) DV = fma(S[aa][c][i], b[aa], fma(g[aa][i], Db[c][aa], DV));
+      for (int aa = 0; aa < 3; ++aa) DV = fma(Sd[aa][c][i], b[aa], fma(g[aa][i], Db[c][aa], DV));
       DB[c][i] = (DV - V[i] * Dd * r) * r;
     }
   }
@@ -503,11 +572,13 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int m, int i0,
   u[0] = J[1] * B[2] - J[2] * B[1];
   u[1] = J[2] * B[0] - J[0] * B[2];
   u[2] = J[0] * B[1] - J[1] * B[0];
-  emit<T, C, FINAL>(a, n, u, J, B, d, dout, st, diag, acc);
+  emit<T, C, FINAL>(a, stage, n, u, J, B, d, dout, st, diag, acc);
 }
 
-template <typename T, typename C, bool FINAL, int MINB>
+// Stage S (0..5) of Cash-Karp with the direct current.
+template <typename T, typename C, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a) {
+  constexpr bool FINAL = S == 5;
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -518,17 +589,28 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
   const int cur = st->cur;
   const T* d = a.d[cur];
   T* dout = const_cast<T*>(a.d[cur ^ 1]);
-  C ca[5];
+  C ca[S > 0 ? S : 1];
 #pragma unroll
-  for (int j = 0; j < 5; ++j) ca[j] = j < a.stage ? coef_a<C>(st, a.stage, j) : (C)0;
+  for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
   const bool diag = a.diag != 0;
   Acc acc;
-  for (int q = k0 - 1; q <= k0; ++q)
-    if (q >= 0) load_plane<T, C, DW, DH, 1>(a, d, ca, q, i0, j0, xs + (q % 3) * 3 * DP);
+  LoadPts<DW, DH, 1> pts;
+  pts.init(i0, j0, a.nx, a.ny);
+  using Raw = PlaneRaw<T, C, S, LoadPts<DW, DH, 1>::LP>;
+  for (int q = k0 - 1; q <= k0; ++q) {
+    if (q < 0) continue;
+    Raw raw;
+    raw.issue(a, d, pts.off, q);
+    raw.template commit<DP>(ca, pts.off, xs + (q % 3) * 3 * DP);
+  }
   for (int m = k0; m < k1; ++m) {
-    load_plane<T, C, DW, DH, 1>(a, d, ca, m + 1, i0, j0, xs + ((m + 1) % 3) * 3 * DP);
+    if (m + 1 < a.nz) {
+      Raw raw;
+      raw.issue(a, d, pts.off, m + 1);
+      raw.template commit<DP>(ca, pts.off, xs + ((m + 1) % 3) * 3 * DP);
+    }
     __syncthreads();
-    direct_out<T, C, FINAL>(a, m, i0, j0, xs, d, dout, st, diag, acc);
+    direct_out<T, C, FINAL>(a, S, m, i0, j0, xs, d, dout, st, diag, acc);
     __syncthreads();
   }
   write_partials<T, C>(a, FINAL, diag, acc, red);
@@ -537,8 +619,64 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
 // ------------------------------------------------------------ launchers
 
 inline size_t stage_smem_bytes(int curl, size_t csize) {
-  return curl == 0 ? (size_t)(4 * 3 * XP + 3 * 4 * BP) * csize
+  return curl == 0 ? (size_t)(XRING * 3 * XP + BRING * 4 * BP) * csize
                    : (size_t)(3 * 3 * DP) * csize;
+}
+
+// Launch stage `stage` (0..5) of the current `CURL` (0 mimetic, 1 direct).
+template <typename T, typename C, int CURL, int MINB>
+cudaError_t launch_stage_t(const StageArgs<T>& a, int stage, dim3 grid, cudaStream_t s) {
+  const size_t smem = stage_smem_bytes(CURL, sizeof(C));
+#define GLEMUR_STAGE_CASE(SS)                                              \
+  case SS:                                                                 \
+    if (CURL == 0)                                                         \
+      k_stage_mimetic<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);           \
+    else                                                                   \
+      k_stage_direct<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);            \
+    break;
+  switch (stage) {
+    GLEMUR_STAGE_CASE(0)
+    GLEMUR_STAGE_CASE(1)
+    GLEMUR_STAGE_CASE(2)
+    GLEMUR_STAGE_CASE(3)
+    GLEMUR_STAGE_CASE(4)
+    GLEMUR_STAGE_CASE(5)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef GLEMUR_STAGE_CASE
+  return cudaGetLastError();
+}
+
+template <typename T, typename C, int CURL, int MINB>
+cudaError_t prepare_stage_t() {
+  const int sm = (int)stage_smem_bytes(CURL, sizeof(C));
+  cudaError_t e = cudaSuccess;
+#define GLEMUR_PREP(SS)                                                                  \
+  if (e == cudaSuccess)                                                                  \
+    e = CURL == 0 ? cudaFuncSetAttribute(k_stage_mimetic<T, C, SS, MINB>,                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm) \
+                  : cudaFuncSetAttribute(k_stage_direct<T, C, SS, MINB>,                 \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  GLEMUR_PREP(0)
+  GLEMUR_PREP(1)
+  GLEMUR_PREP(2)
+  GLEMUR_PREP(3)
+  GLEMUR_PREP(4)
+  GLEMUR_PREP(5)
+#undef GLEMUR_PREP
+  return e;
+}
+
+template <typename T, typename C, int CURL, int MINB>
+int stage_ctas_per_sm_t() {
+  int n = 0;
+  const size_t s = stage_smem_bytes(CURL, sizeof(C));
+  if (CURL == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_mimetic<T, C, 3, MINB>, NT, s);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_direct<T, C, 3, MINB>, NT, s);
+  return n;
 }
 
 }  // namespace glemur
