@@ -97,6 +97,16 @@ __device__ __forceinline__ C dot3(const C a[3], const C b[3]) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// 1/det: IEEE division in FP64; in mixed precision the determinant is
+// already carried beyond FP32 and the reciprocal only scales FP32 data, so
+// the fast reciprocal (about 2 ulp) is used.
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+__device__ __forceinline__ float recip(float v) { return __fdividef(1.0f, v); }
+
+__device__ __forceinline__ float nanmaxf_(float a, float b) {
+  return (a > b || a != a) ? a : b;
+}
+
 template <typename C>
 __device__ __forceinline__ C coef_a(const DevState* st, int s, int j);
 template <>
@@ -167,9 +177,30 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   return v;
 }
 
-// Per-CTA accumulators of the diagnostic and error reductions.
-struct Acc {
+// Per-thread accumulators of the diagnostic and error reductions, reduced
+// per CTA in FP64.  FP64 mode accumulates in double; mixed precision keeps
+// the energy sum as a compensated float pair (error-free additions) and the
+// maxima in float, so no per-node work lands on the FP64 pipe.
+template <typename C>
+struct Acc;
+template <>
+struct Acc<double> {
   double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
+  __device__ __forceinline__ void add_e(double w) { e += w; }
+  __device__ __forceinline__ void max_lam(double v) { lam = nanmax(lam, v); }
+  __device__ __forceinline__ double e_total() const { return e; }
+};
+template <>
+struct Acc<float> {
+  float eh = 0.0f, el = 0.0f, lam = 0.0f, xi2 = 0.0f, xis2 = 0.0f;
+  __device__ __forceinline__ void add_e(float w) {
+    float s, err;
+    two_sum(eh, w, s, err);
+    eh = s;
+    el += err;
+  }
+  __device__ __forceinline__ void max_lam(float v) { lam = nanmaxf_(lam, v); }
+  __device__ __forceinline__ double e_total() const { return (double)eh + (double)el; }
 };
 
 // ------------------------------------------------------------ x_s planes
@@ -236,6 +267,35 @@ struct PlaneRaw {
 
 // ------------------------------------------------------------ mimetic
 
+// The B-tile points this thread computes (tile + halo 1, at most BPT), with
+// everything about them that does not change from plane to plane: the x
+// tile index, the in-plane node offset, the x/y stencil (0 central, 1 lower
+// face, 2 upper face), whether the node is the tile's own (energy sum), and
+// how many of its x/y index coordinates lie on the boundary (zeta).
+struct BPts {
+  static constexpr int BPT = (BP + NT - 1) / NT;
+  int x0[BPT], nxy[BPT], code[BPT];
+  __device__ __forceinline__ void init(int i0, int j0, int nx, int ny) {
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+      const int p = threadIdx.x + t * NT;
+      x0[t] = -1;
+      nxy[t] = 0;
+      code[t] = 0;
+      if (p >= BP) continue;
+      const int bx = p % BW, by = p / BW;
+      const int gi = i0 - 1 + bx, gj = j0 - 1 + by;
+      if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
+      x0[t] = (by + 1) * XW + (bx + 1);
+      nxy[t] = gj * nx + gi;
+      const int sx = gi == 0 ? 1 : (gi == nx - 1 ? 2 : 0);
+      const int sy = gj == 0 ? 1 : (gj == ny - 1 ? 2 : 0);
+      const int own = bx >= 1 && bx <= TX && by >= 1 && by <= TY;
+      code[t] = sx | (sy << 2) | (own << 4) | (((sx != 0) + (sy != 0)) << 5);
+    }
+  }
+};
+
 constexpr int XRING = 6;  // planes of x_s in shared memory
 constexpr int BRING = 4;  // planes of B (+ 1/det G) in shared memory
 
@@ -245,10 +305,10 @@ __device__ __forceinline__ int bslot(int q) { return (q + BRING) % BRING; }
 // B (and 1/det G) at every node of plane q in the tile + halo 1.  Index-space
 // differences: central inside, second-order one-sided on boundary faces.
 template <typename T, typename C>
-__device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, int j0,
-                                          int k0, int k1, const C* __restrict__ xs,
+__device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, int k1,
+                                          const BPts& bp, const C* __restrict__ xs,
                                           C* __restrict__ bs, bool diag, bool state,
-                                          double& eacc) {
+                                          Acc<C>& acc) {
   const int N = a.nx * a.ny * a.nz;
   const C* xq = xs + xslot(q) * 3 * XP;
   const C* xm = xs + xslot(q - 1) * 3 * XP;
@@ -257,34 +317,29 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
   const C* xp2 = xs + xslot(q + 2) * 3 * XP;
   C* bq = bs + bslot(q) * 4 * BP;
   const C h20 = h2of<T, C>(a, 0), h21 = h2of<T, C>(a, 1), h22 = h2of<T, C>(a, 2);
-  const bool zlo = q == 0, zhi = q == a.nz - 1;
-  for (int p = threadIdx.x; p < BP; p += NT) {
-    const int bx = p % BW, by = p / BW;
-    const int gi = i0 - 1 + bx, gj = j0 - 1 + by;
-    if (gi < 0 || gi >= a.nx || gj < 0 || gj >= a.ny) continue;
-    const int x0 = (by + 1) * XW + (bx + 1);
+  const int sz = q == 0 ? 1 : (q == a.nz - 1 ? 2 : 0);
+  const int nq = q * a.nx * a.ny;
+  const bool own_plane = diag && q >= k0 && q < k1;
+#pragma unroll
+  for (int t = 0; t < BPts::BPT; ++t) {
+    const int x0 = bp.x0[t];
+    if (x0 < 0) continue;
+    const int p = threadIdx.x + t * NT;
+    const int code = bp.code[t];
+    const int sx = code & 3, sy = (code >> 2) & 3;
     C g[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const C* s = xq + c * XP;
-      if (gi > 0 && gi < a.nx - 1)
-        g[0][c] = s[x0 + 1] - s[x0 - 1];
-      else if (gi == 0)
-        g[0][c] = ((C)4 * s[x0 + 1] - (C)3 * s[x0]) - s[x0 + 2];
-      else
-        g[0][c] = ((C)3 * s[x0] - (C)4 * s[x0 - 1]) + s[x0 - 2];
-      if (gj > 0 && gj < a.ny - 1)
-        g[1][c] = s[x0 + XW] - s[x0 - XW];
-      else if (gj == 0)
-        g[1][c] = ((C)4 * s[x0 + XW] - (C)3 * s[x0]) - s[x0 + 2 * XW];
-      else
-        g[1][c] = ((C)3 * s[x0] - (C)4 * s[x0 - XW]) + s[x0 - 2 * XW];
-      if (!zlo && !zhi)
-        g[2][c] = xp[c * XP + x0] - xm[c * XP + x0];
-      else if (zlo)
-        g[2][c] = ((C)4 * xp[c * XP + x0] - (C)3 * s[x0]) - xp2[c * XP + x0];
-      else
-        g[2][c] = ((C)3 * s[x0] - (C)4 * xm[c * XP + x0]) + xm2[c * XP + x0];
+      g[0][c] = sx == 0 ? s[x0 + 1] - s[x0 - 1]
+              : sx == 1 ? ((C)4 * s[x0 + 1] - (C)3 * s[x0]) - s[x0 + 2]
+                        : ((C)3 * s[x0] - (C)4 * s[x0 - 1]) + s[x0 - 2];
+      g[1][c] = sy == 0 ? s[x0 + XW] - s[x0 - XW]
+              : sy == 1 ? ((C)4 * s[x0 + XW] - (C)3 * s[x0]) - s[x0 + 2 * XW]
+                        : ((C)3 * s[x0] - (C)4 * s[x0 - XW]) + s[x0 - 2 * XW];
+      g[2][c] = sz == 0 ? xp[c * XP + x0] - xm[c * XP + x0]
+              : sz == 1 ? ((C)4 * xp[c * XP + x0] - (C)3 * s[x0]) - xp2[c * XP + x0]
+                        : ((C)3 * s[x0] - (C)4 * xm[c * XP + x0]) + xm2[c * XP + x0];
     }
     g[0][0] += h20;
     g[1][1] += h21;
@@ -292,8 +347,8 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
     const C det = det3(g[0], g[1], g[2]);
     if (det <= (C)0)  // NaN: reported by the error norm
       atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
-    const C r = (C)1 / det;
-    const int n = (q * a.ny + gj) * a.nx + gi;
+    const C r = recip(det);
+    const int n = nq + bp.nxy[t];
     const C b0 = (C)__ldg(&a.B0s[n]), b1 = (C)__ldg(&a.B0s[N + n]),
             b2 = (C)__ldg(&a.B0s[2 * N + n]);
     C B[3];
@@ -303,13 +358,11 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int i0, 
       bq[c * BP + p] = B[c];
     }
     bq[3 * BP + p] = r;
-    if (diag && q >= k0 && q < k1 && bx >= 1 && bx <= TX && by >= 1 && by <= TY) {
+    if (own_plane && (code & 16)) {
       // eq. "magnetic energy": zeta halves per boundary index coordinate
-      double zeta = 1.0;
-      if (gi == 0 || gi == a.nx - 1) zeta *= 0.5;
-      if (gj == 0 || gj == a.ny - 1) zeta *= 0.5;
-      if (zlo || zhi) zeta *= 0.5;
-      eacc += zeta * (double)dot3(B, B) * (double)det;
+      const int nb = ((code >> 5) & 3) + (sz != 0);
+      const C zeta = nb == 0 ? (C)1 : nb == 1 ? (C)0.5 : nb == 2 ? (C)0.25 : (C)0.125;
+      acc.add_e(zeta * dot3(B, B) * det);
     }
   }
 }
@@ -319,15 +372,14 @@ template <typename T, typename C, bool FINAL>
 __device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, const C u[3],
                                      const C J[3], const C B[3], const T* __restrict__ d,
                                      T* __restrict__ dout, const DevState* st, bool diag,
-                                     Acc& acc) {
+                                     Acc<C>& acc) {
   const int N = a.nx * a.ny * a.nz;
   if (diag) {
-    const double u2 = (double)dot3(u, u), b2 = (double)dot3(B, B),
-                 j2 = (double)dot3(J, J);
+    const C u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
     // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
     if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
-    const double jb = j2 * b2;
-    if (jb > 1e-300 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+    const C jb = j2 * b2;
+    if (jb > (C)0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
   }
   if (!FINAL) {
     T* ko = a.k[stage];
@@ -353,7 +405,7 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, co
       er = fma(e4, k5, er);
       er = fma(e5, u[c], er);
       dout[c * N + n] = (T)((C)__ldg(&d[c * N + n]) + up);
-      acc.lam = nanmax(acc.lam, (double)fabs(er));
+      acc.max_lam(fabs(er));
     }
   }
 }
@@ -363,7 +415,7 @@ template <typename T, typename C, bool FINAL>
 __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, int m, int i0,
                                             int j0, const C* __restrict__ xs,
                                             const C* __restrict__ bs, const T* d, T* dout,
-                                            const DevState* st, bool diag, Acc& acc) {
+                                            const DevState* st, bool diag, Acc<C>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gi = i0 + tx, gj = j0 + ty;
   if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
@@ -406,18 +458,18 @@ __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, in
 
 template <typename T, typename C>
 __device__ __forceinline__ void write_partials(const StageArgs<T>& a, bool final_stage,
-                                               bool diag, Acc& acc, double* red) {
+                                               bool diag, Acc<C>& acc, double* red) {
   const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   if (final_stage) {
-    const double v = block_reduce<true>(acc.lam, red);
+    const double v = block_reduce<true>((double)acc.lam, red);
     if (threadIdx.x == 0) a.part[PART_LAMBDA * a.nblocks + bid] = v;
   }
   if (diag) {
-    double v = block_reduce<false>(acc.e, red);
+    double v = block_reduce<false>(acc.e_total(), red);
     if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
-    v = block_reduce<true>(acc.xi2, red);
+    v = block_reduce<true>((double)acc.xi2, red);
     if (threadIdx.x == 0) a.part[PART_XI2 * a.nblocks + bid] = v;
-    v = block_reduce<true>(acc.xis2, red);
+    v = block_reduce<true>((double)acc.xis2, red);
     if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
   }
 }
@@ -441,9 +493,11 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
 #pragma unroll
   for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
   const bool diag = a.diag != 0;
-  Acc acc;
+  Acc<C> acc;
   LoadPts<XW, XH, 2> pts;
   pts.init(i0, j0, a.nx, a.ny);
+  BPts bp;
+  bp.init(i0, j0, a.nx, a.ny);
   using Raw = PlaneRaw<T, C, S, LoadPts<XW, XH, 2>::LP>;
   // prologue: stage input planes k0-2 .. k0+3, then B at k0-1 .. k0+1
   for (int q = k0 - 2; q <= k0 + 3; ++q) {
@@ -455,7 +509,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
   __syncthreads();
   for (int q = k0 - 1; q <= k0 + 1; ++q)
     if (q >= 0 && q < a.nz && q <= k1)
-      compute_B<T, C>(a, q, i0, j0, k0, k1, xs, bs, diag, S == 0, acc.e);
+      compute_B<T, C>(a, q, k0, k1, bp, xs, bs, diag, S == 0, acc);
   __syncthreads();
   for (int m = k0; m < k1; ++m) {
     const int qn = m + 4;  // stage input plane loaded in this iteration
@@ -464,7 +518,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
     if (load) raw.issue(a, d, pts.off, qn);
     const int qb = m + 2;  // B plane computed in this iteration
     if (qb < a.nz && qb <= k1)
-      compute_B<T, C>(a, qb, i0, j0, k0, k1, xs, bs, diag, S == 0, acc.e);
+      compute_B<T, C>(a, qb, k0, k1, bp, xs, bs, diag, S == 0, acc);
     mimetic_out<T, C, FINAL>(a, S, m, i0, j0, xs, bs, d, dout, st, diag, acc);
     if (load) raw.template commit<XP>(ca, pts.off, xs + xslot(qn) * 3 * XP);
     __syncthreads();
@@ -477,7 +531,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
 template <typename T, typename C, bool FINAL>
 __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int m, int i0,
                                            int j0, const C* __restrict__ xs, const T* d,
-                                           T* dout, const DevState* st, bool diag, Acc& acc) {
+                                           T* dout, const DevState* st, bool diag,
+                                           Acc<C>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gi = i0 + tx, gj = j0 + ty;
   if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
@@ -534,7 +589,7 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int
   const C det = det3(g[0], g[1], g[2]);
   if (det <= (C)0)  // NaN: reported by the error norm
     atomicOr(&a.st->flags, stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
-  const C r = (C)1 / det;
+  const C r = recip(det);
   C V[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) V[i] = g[0][i] * b[0] + g[1][i] * b[1] + g[2][i] * b[2];
@@ -593,7 +648,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
 #pragma unroll
   for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
   const bool diag = a.diag != 0;
-  Acc acc;
+  Acc<C> acc;
   LoadPts<DW, DH, 1> pts;
   pts.init(i0, j0, a.nx, a.ny);
   using Raw = PlaneRaw<T, C, S, LoadPts<DW, DH, 1>::LP>;
