@@ -206,7 +206,10 @@ def braid_regions(n_regions: int, seed: int | None, amp_alternating: bool,
 
 
 def braid_field(X, regions, background=(0.0, 0.0, 1.0)):
-    B = np.zeros_like(X)
+    # complex parameters give a complex field (derivatives by complex step)
+    dtype = np.result_type(X, *[complex(v) if isinstance(v, complex) else float(v)
+                                 for r in regions for v in r])
+    B = np.zeros(X.shape, dtype=dtype)
     for c in range(3):
         B[c] += background[c]
     for (xc, yc, zc, k, l, L) in regions:

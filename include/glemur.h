@@ -102,6 +102,7 @@ typedef struct {
   double xi;            /* xi = max |J x B| / B^2 of that state */
   double xi_sin;        /* max |J x B| / (|J| |B|) of that state */
   int status;           /* GLEMUR_OK or the error that stopped stepping */
+  double dt_last;       /* size of the last accepted step (replay schedules) */
 } glemur_stats;
 
 /* Fill *o with the defaults listed in glemur_opts. */
@@ -135,6 +136,20 @@ int glemur_set_B0(glemur_ctx* ctx, const double* B0, int mem);
 
 /* Copy the current accepted positions x into `x` (float64 field). */
 int glemur_get_x(glemur_ctx* ctx, double* x, int mem);
+
+/* Bytes of the raw relaxation state (the displacement x - X of every node
+ * in the context's storage precision: 3N doubles, or 3N floats in mixed
+ * precision); 0 for NULL. */
+size_t glemur_state_bytes(const glemur_ctx* ctx);
+
+/* Copy the raw state into dev_buf (device memory of glemur_state_bytes()):
+ * an exact checkpoint, unlike glemur_get_x whose float64 x = X + d rounds. */
+int glemur_get_state(glemur_ctx* ctx, void* dev_buf);
+
+/* Restore a raw state taken by glemur_get_state from a context of the same
+ * grid and precision.  Like glemur_set_x it resets the counters, the time,
+ * the error status and dt = dt0. */
+int glemur_set_state(glemur_ctx* ctx, const void* dev_buf);
 
 /* Frictional velocity u = J x B of the current state at every node (0 on
  * the boundary) into `u` (float64 field): the right-hand side of eq. "x
@@ -186,6 +201,44 @@ int glemur_kernels_per_attempt(const glemur_ctx* ctx);
  * the step control), n = glemur_kernels_per_attempt(ctx) <= cap.  Returns n,
  * or a negative error (BADARG if cap < n). */
 int glemur_profile_attempt(glemur_ctx* ctx, float* ms, int cap);
+
+/* ---- adjoint (reverse mode) of the relaxation, mimetic current ---------
+ * The step of section "Time Stepping" at a fixed step size is a smooth map
+ * x_{n+1} = Phi(x_n; B0); these calls give its vector-Jacobian products so
+ * that gradients of a loss of the final state with respect to B0 (and hence
+ * to any parameters of B0) follow by running the steps backwards with
+ * recomputation.  The paper relaxes fields and does not differentiate the
+ * relaxation; these entry points are this library's addition.  All fields
+ * are float64 device arrays (layout above); the adjoint workspace is
+ * caller-owned device memory (256-byte aligned) of
+ * glemur_adjoint_workspace_bytes().  They synchronise the stream and leave
+ * the context's pending step size set to the dt they used. */
+
+enum glemur_loss { GLEMUR_LOSS_ENERGY = 0, GLEMUR_LOSS_XI = 1 };
+
+/* Adjoint workspace bytes for an nx*ny*nz grid (0 for invalid sizes). */
+size_t glemur_adjoint_workspace_bytes(int nx, int ny, int nz, int precision);
+
+/* With the context at state x_n: lam = (d x_{n+1} / d x_n)^T lam_next and
+ * mu_B0 += (d x_{n+1} / d B0)^T lam_next for one Cash-Karp step of size dt
+ * (the stages are recomputed from x_n).  Boundary entries of lam are zero
+ * (line-tied nodes are not variables).  lam and lam_next may not alias.
+ * Errors: BADARG (also for the direct current), WORKSPACE, CUDA. */
+int glemur_vjp_step(glemur_ctx* ctx, double dt, const double* lam_next, double* lam,
+                    double* mu_B0, void* adj_ws, size_t adj_bytes);
+
+/* Loss of the current state -- GLEMUR_LOSS_ENERGY: E_M (eq. "magnetic
+ * energy"); GLEMUR_LOSS_XI: xi = max |J x B| / B^2, differentiated at its
+ * argmax node -- into *value (host), its gradient with respect to the
+ * positions into lam (overwritten) and with respect to B0 added to mu_B0. */
+int glemur_loss_grad(glemur_ctx* ctx, int loss, double* value, double* lam, double* mu_B0,
+                     void* adj_ws, size_t adj_bytes);
+
+/* out[p] = sum_m dB0[p*m_len + m] * mu[m] for p < n_params (device arrays):
+ * the gradient with respect to parameters theta of B0(theta) from the
+ * field adjoint mu_B0 and dB0/dtheta.  Asynchronous on `stream`. */
+int glemur_param_contract(int n_params, long long m_len, const double* dB0, const double* mu,
+                          double* out, void* stream);
 
 /* Largest grid (nodes) glemur_energy_static accepts: 256^3. */
 #define GLEMUR_STATIC_MAX_NODES (1LL << 24)

@@ -87,6 +87,9 @@ def lib():
         L.ora_step_fixed.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, C.c_double, _dp]
         L.ora_energy.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
         L.ora_forcefree.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_velocity.argtypes = [C.POINTER(_Grid), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_relax_loss.argtypes = [C.POINTER(_Grid), C.c_void_p, C.c_void_p, _dp, C.c_int,
+                                     C.c_int, C.c_void_p]
         _lib = L
     return _lib
 
@@ -236,3 +239,35 @@ def forcefree(grid, x, B0, curl=MIMETIC):
     a, b = np.zeros(1), np.zeros(1)
     rc = lib().ora_forcefree(C.byref(_g(grid)), curl, _p(x), _p(B0), _p(a), _p(b))
     return float(a[0]), float(b[0]), rc
+
+
+# ---------------------------------------------------------------- complex step
+# Complex-analytic evaluation of the same method (glemur_oracle_cstep.c):
+# with an input perturbed by i*h, Im(output)/h is its exact derivative.
+
+CSTEP_H = 1e-30
+LOSS_ENERGY, LOSS_XI = 0, 1
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def cs_velocity(grid, y, B0):
+    """u(y; B0) with complex positions and field (mimetic current)."""
+    y, B0 = _c(y), _c(B0)
+    u = np.zeros((3, grid.nz, grid.ny, grid.nx), dtype=np.complex128)
+    rc = lib().orc_velocity(C.byref(_g(grid)), y.ctypes.data, B0.ctypes.data, u.ctypes.data)
+    return u, rc
+
+
+def cs_relax_loss(grid, x0, B0, dts, loss=LOSS_ENERGY):
+    """Cash-Karp steps at the schedule `dts` from x0, then the loss
+    (E_M or xi) of the final state; complex in, complex out."""
+    x = _c(x0).copy()
+    B0 = _c(B0)
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    val = np.zeros(1, dtype=np.complex128)
+    rc = lib().orc_relax_loss(C.byref(_g(grid)), x.ctypes.data, B0.ctypes.data,
+                              d.ctypes.data_as(_dp), len(d), loss, val.ctypes.data)
+    return complex(val[0]), x, rc

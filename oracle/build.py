@@ -12,6 +12,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "glemur_oracle.c")
+SRC_CS = os.path.join(HERE, "glemur_oracle_cstep.c")
 HDR = os.path.join(HERE, "glemur_oracle.h")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
@@ -21,11 +22,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle if the library is missing or older than its source."""
     os.makedirs(OUT_DIR, exist_ok=True)
     stale = force or not os.path.exists(LIB) or any(
-        os.path.getmtime(p) > os.path.getmtime(LIB) for p in (SRC, HDR, __file__))
+        os.path.getmtime(p) > os.path.getmtime(LIB) for p in (SRC, SRC_CS, HDR, __file__))
     if stale:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-               "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+               "-Wall", "-Wextra", "-o", tmp, SRC, SRC_CS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB

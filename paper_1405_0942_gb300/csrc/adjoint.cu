@@ -1,0 +1,622 @@
+// Hand-written adjoint (reverse mode) of the relaxation step, FP64.
+//
+// Forward (one Cash-Karp step of fixed size dt, section "Time Stepping"):
+//   y_s = x + dt sum_{j<s} a_sj k_j,  k_s = f(y_s; B0),
+//   x' = x + dt sum_j b_j k_j,
+// with f(y)_n = J_n x B_n at interior nodes (eq. "magneto friction"),
+// B = G B0s / det G at every node (eq. "B transformation" in index-space
+// form), and the compact mimetic current J = (c_0 g_0 + c_1 g_1 + c_2 g_2) /
+// det G, c_a = P_{a+1}.g_{a+2} - P_{a+2}.g_{a+1}, g_a and P_a the central
+// differences of y and B (section "Mimetic Operators").
+//
+// Reverse: given lam' = dL/dx', lam_k_j = dt b_j lam', and for s = 6..1 the
+// stage VJP lam_y = (df/dy)^T lam_k_s, mu += (df/dB0s)^T lam_k_s, then
+// lam_k_j += dt a_sj lam_y (j < s) and lam += lam_y; finally lam += lam'.
+// The stage VJP runs as node-local kernels and gathers (no atomics):
+//   1. reverse of u = J x B and of the current at each interior node ->
+//      per-node adjoints of P_a, g_a, 1/det G and the centre B;
+//   2. at every node, gather the adjoint of B from the P adjoints of its
+//      interior neighbours, reverse the pull-back -> adjoint of g_a, mu;
+//   3. at every node, gather the adjoint of y from the g_a adjoints of the
+//      nodes whose difference stencils contain it (central inside, one-sided
+//      on boundary faces).
+// Boundary nodes are line-tied: their position adjoint is not propagated.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+
+#include "glemur.h"
+#include "glemur_dev.cuh"
+
+namespace glemur {
+
+// Cash-Karp table (Cash & Karp, ACM TOMS 16, 1990) for the reverse combine.
+__constant__ double AD_A[6][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0, 0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0, 0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0,
+     0}};
+__constant__ double AD_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0,
+                                512.0 / 1771.0};
+
+struct AdjGeom {
+  int nx, ny, nz;
+  double h2[3];  // 2 h_a
+  double s[3];   // B0s_a = B0_a s_a
+};
+
+__device__ __forceinline__ int stencil(int i, int n) {  // 0 central, 1 lower, 2 upper
+  return i == 0 ? 1 : (i == n - 1 ? 2 : 0);
+}
+
+// Column a of G = index-space differences of y (displacement) + 2 h_a e_a.
+template <typename T>
+__device__ __forceinline__ void gcol(const AdjGeom& g, const T* y, int N, int a, int i, int j,
+                                     int k, double out[3]) {
+  const int id[3] = {i, j, k};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  const int c0 = (k * g.ny + j) * g.nx + i;
+  const int sa = st[a];
+  const int kind = stencil(id[a], n[a]);
+  for (int c = 0; c < 3; ++c) {
+    const T* v = y + c * N;
+    double d;
+    if (kind == 0)
+      d = (double)v[c0 + sa] - (double)v[c0 - sa];
+    else if (kind == 1)
+      d = (4.0 * (double)v[c0 + sa] - 3.0 * (double)v[c0]) - (double)v[c0 + 2 * sa];
+    else
+      d = (3.0 * (double)v[c0] - 4.0 * (double)v[c0 - sa]) + (double)v[c0 - 2 * sa];
+    out[c] = d;
+  }
+  out[a] += g.h2[a];
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double dot(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+#define NODE_LOOP(N)                                                                      \
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (N); n += gridDim.x * blockDim.x)
+
+// y = d + sum_{j<s} dt a_sj k_j (stage input as a displacement), all nodes.
+template <typename T>
+__global__ void k_adj_stage_input(int N3, const T* d, const T* const* k, int s, double dt,
+                                  double* y) {
+  NODE_LOOP(N3) {
+    double v = (double)d[n];
+    for (int j = 0; j < s; ++j) v += dt * AD_A[s][j] * (double)k[j][n];
+    y[n] = v;
+  }
+}
+
+// B = G B0s / det G and 1/det G at every node of the stage input y.
+template <typename T>
+__global__ void k_adj_fwd_B(AdjGeom g, const double* y, const T* B0s, double* Bb, double* rb) {
+  const int N = g.nx * g.ny * g.nz;
+  NODE_LOOP(N) {
+    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+    double G[3][3];
+    for (int a = 0; a < 3; ++a) gcol(g, y, N, a, i, j, k, G[a]);
+    double m[3];
+    cross3(G[1], G[2], m);
+    const double r = 1.0 / dot(G[0], m);
+    const double b0 = (double)B0s[n], b1 = (double)B0s[N + n], b2 = (double)B0s[2 * N + n];
+    for (int c = 0; c < 3; ++c) Bb[c * N + n] = (G[0][c] * b0 + G[1][c] * b1 + G[2][c] * b2) * r;
+    rb[n] = r;
+  }
+}
+
+__device__ __forceinline__ bool interior(const AdjGeom& g, int i, int j, int k) {
+  return i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+}
+
+// Forward current at an interior node from y and the B buffer.
+__device__ __forceinline__ void current_at(const AdjGeom& g, const double* y, const double* Bb,
+                                           const double* rb, int n, int i, int j, int k,
+                                           double G[3][3], double P[3][3], double cc[3],
+                                           double V[3], double J[3]) {
+  const int N = g.nx * g.ny * g.nz;
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  for (int a = 0; a < 3; ++a) {
+    gcol(g, y, N, a, i, j, k, G[a]);
+    for (int c = 0; c < 3; ++c) P[a][c] = Bb[c * N + n + st[a]] - Bb[c * N + n - st[a]];
+  }
+  cc[0] = dot(P[1], G[2]) - dot(P[2], G[1]);
+  cc[1] = dot(P[2], G[0]) - dot(P[0], G[2]);
+  cc[2] = dot(P[0], G[1]) - dot(P[1], G[0]);
+  const double r = rb[n];
+  for (int c = 0; c < 3; ++c) {
+    V[c] = cc[0] * G[0][c] + cc[1] * G[1][c] + cc[2] * G[2][c];
+    J[c] = V[c] * r;
+  }
+}
+
+// Step 1: reverse of u = J x B and of the current at interior nodes.
+// lam_u: adjoint of the stage velocity (3N).  Outputs (zero off the
+// interior): lamP [3 axes][3 comp][N], lamg [3][3][N] (current part),
+// lamr [N] (adjoint of 1/det G from the current), lamB [3][N] (centre B).
+__global__ void k_adj_current(AdjGeom g, const double* y, const double* Bb, const double* rb,
+                              const double* lam_u, double* lamP, double* lamg, double* lamr,
+                              double* lamB) {
+  const int N = g.nx * g.ny * g.nz;
+  NODE_LOOP(N) {
+    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+    double lP[3][3] = {{0}}, lg[3][3] = {{0}}, lr = 0.0, lB[3] = {0, 0, 0};
+    if (interior(g, i, j, k)) {
+      double G[3][3], P[3][3], cc[3], V[3], J[3];
+      current_at(g, y, Bb, rb, n, i, j, k, G, P, cc, V, J);
+      const double r = rb[n];
+      const double lu[3] = {lam_u[n], lam_u[N + n], lam_u[2 * N + n]};
+      const double B[3] = {Bb[n], Bb[N + n], Bb[2 * N + n]};
+      double lJ[3];
+      cross3(B, lu, lJ);  // u = J x B: lam_J = B x lam_u, lam_B = lam_u x J
+      cross3(lu, J, lB);
+      double lV[3];
+      for (int c = 0; c < 3; ++c) lV[c] = lJ[c] * r;
+      lr = dot(lJ, V);
+      double lc[3];
+      for (int a = 0; a < 3; ++a) {
+        lc[a] = dot(lV, G[a]);
+        for (int c = 0; c < 3; ++c) lg[a][c] += cc[a] * lV[c];
+      }
+      // c_a = P_{a+1} . g_{a+2} - P_{a+2} . g_{a+1}
+      for (int a = 0; a < 3; ++a) {
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        for (int c = 0; c < 3; ++c) {
+          lP[a1][c] += lc[a] * G[a2][c];
+          lg[a2][c] += lc[a] * P[a1][c];
+          lP[a2][c] -= lc[a] * G[a1][c];
+          lg[a1][c] -= lc[a] * P[a2][c];
+        }
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        lamP[(a * 3 + c) * N + n] = lP[a][c];
+        lamg[(a * 3 + c) * N + n] = lg[a][c];
+      }
+    lamr[n] = lr;
+    for (int c = 0; c < 3; ++c) lamB[c * N + n] = lB[c];
+  }
+}
+
+// Step 2: gather the adjoint of B, reverse the pull-back, add the energy
+// loss (weight wE; E_M = sum zeta |G B0s|^2 / det G / 16) and the current's
+// g and 1/det adjoints.  lamg is updated in place to the total adjoint of
+// the columns g_a; mu (adjoint of B0s) is accumulated.
+template <typename T>
+__global__ void k_adj_pullback(AdjGeom g, const double* y, const T* B0s, const double* rb,
+                               const double* lamP, double* lamg, const double* lamr,
+                               const double* lamB, double wE, double* mu) {
+  const int N = g.nx * g.ny * g.nz;
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  NODE_LOOP(N) {
+    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+    const int id[3] = {i, j, k};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    // adjoint of B(n): the centre term plus, since P_a(m) = B(m + e_a) -
+    // B(m - e_a), +lamP_a(n - e_a) and -lamP_a(n + e_a) (zero unless that
+    // neighbour is interior).
+    double lB[3] = {lamB[n], lamB[N + n], lamB[2 * N + n]};
+    for (int a = 0; a < 3; ++a) {
+      if (id[a] - 1 >= 0)
+        for (int c = 0; c < 3; ++c) lB[c] += lamP[(a * 3 + c) * N + n - st[a]];
+      if (id[a] + 1 < ext[a])
+        for (int c = 0; c < 3; ++c) lB[c] -= lamP[(a * 3 + c) * N + n + st[a]];
+    }
+    double G[3][3];
+    for (int a = 0; a < 3; ++a) gcol(g, y, N, a, i, j, k, G[a]);
+    const double r = rb[n];
+    const double b[3] = {(double)B0s[n], (double)B0s[N + n], (double)B0s[2 * N + n]};
+    double W[3];
+    for (int c = 0; c < 3; ++c) W[c] = G[0][c] * b[0] + G[1][c] * b[1] + G[2][c] * b[2];
+    // B = W r
+    double lW[3];
+    for (int c = 0; c < 3; ++c) lW[c] = lB[c] * r;
+    double lr = dot(lB, W) + lamr[n];
+    if (wE != 0.0) {
+      int nb = (i == 0 || i == g.nx - 1) + (j == 0 || j == g.ny - 1) + (k == 0 || k == g.nz - 1);
+      const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
+      for (int c = 0; c < 3; ++c) lW[c] += wE * zeta * W[c] * r / 8.0;
+      lr += wE * zeta * dot(W, W) / 16.0;
+    }
+    // W = sum_a g_a b_a ; r = 1 / det G, d det / d g_a = g_{a+1} x g_{a+2}
+    const double ldet = -lr * r * r;
+    for (int a = 0; a < 3; ++a) {
+      mu[a * N + n] += dot(lW, G[a]);
+      double cr[3];
+      cross3(G[(a + 1) % 3], G[(a + 2) % 3], cr);
+      for (int c = 0; c < 3; ++c)
+        lamg[(a * 3 + c) * N + n] += b[a] * lW[c] + ldet * cr[c];
+    }
+  }
+}
+
+// Coefficient of y(p) in the difference g_a(m) along axis a (index m of the
+// stencil's node, p of the position), extent n.
+__device__ __forceinline__ double gcoef(int m, int p, int n) {
+  const int kind = stencil(m, n);
+  if (kind == 0) return p == m + 1 ? 1.0 : (p == m - 1 ? -1.0 : 0.0);
+  if (kind == 1) return p == 0 ? -3.0 : (p == 1 ? 4.0 : (p == 2 ? -1.0 : 0.0));
+  return p == n - 1 ? 3.0 : (p == n - 2 ? -4.0 : (p == n - 3 ? 1.0 : 0.0));
+}
+
+// Step 3: adjoint of the stage input at interior nodes (0 on the boundary).
+__global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
+  const int N = g.nx * g.ny * g.nz;
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  NODE_LOOP(N) {
+    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+    const int id[3] = {i, j, k};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    double ly[3] = {0, 0, 0};
+    if (interior(g, i, j, k)) {
+      for (int a = 0; a < 3; ++a)
+        for (int dm = -2; dm <= 2; ++dm) {
+          const int m = id[a] + dm;
+          if (m < 0 || m >= ext[a]) continue;
+          const double w = gcoef(m, id[a], ext[a]);
+          if (w == 0.0) continue;
+          const int nm = n + dm * st[a];
+          for (int c = 0; c < 3; ++c) ly[c] += w * lamg[(a * 3 + c) * N + nm];
+        }
+    }
+    for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+  }
+}
+
+// Reverse Runge-Kutta combine after stage s: lam += lam_y,
+// lam_k_j += dt a_sj lam_y (j < s).
+__global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* lam,
+                         double* const* lam_k) {
+  NODE_LOOP(N3) {
+    const double v = lam_y[n];
+    lam[n] += v;
+    for (int j = 0; j < s; ++j) lam_k[j][n] += dt * AD_A[s][j] * v;
+  }
+}
+
+// Seeds of one step's reverse: lam_k_j = dt b_j lam', lam = lam'.
+__global__ void k_adj_seed(int N3, const double* lam_next, double dt, double* lam,
+                           double* const* lam_k) {
+  NODE_LOOP(N3) {
+    const double v = lam_next[n];
+    lam[n] = v;
+    for (int j = 0; j < 6; ++j) lam_k[j][n] = dt * AD_B5[j] * v;
+  }
+}
+
+// Per-CTA (value, index) of xi = |J x B| / |B|^2 over interior nodes.
+__global__ void k_adj_xi_partial(AdjGeom g, const double* y, const double* Bb, const double* rb,
+                                 double* pv, int* pi) {
+  const int N = g.nx * g.ny * g.nz;
+  double best = -1.0;
+  int arg = -1;
+  NODE_LOOP(N) {
+    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+    if (!interior(g, i, j, k)) continue;
+    double G[3][3], P[3][3], cc[3], V[3], J[3], u[3];
+    current_at(g, y, Bb, rb, n, i, j, k, G, P, cc, V, J);
+    const double B[3] = {Bb[n], Bb[N + n], Bb[2 * N + n]};
+    cross3(J, B, u);
+    const double v = sqrt(dot(u, u)) / dot(B, B);
+    if (v > best || (v == best && n < arg)) {
+      best = v;
+      arg = n;
+    }
+  }
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = arg;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double v2 = sv[threadIdx.x + o];
+      const int i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 >= 0 && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+
+// Seed of the xi loss at its argmax node: lam_u = u / (|u| |B|^2) and the
+// direct B dependence -2 |u| B / |B|^4; writes the value to out[0].
+__global__ void k_adj_xi_seed(AdjGeom g, const double* y, const double* Bb, const double* rb,
+                              const double* pv, const int* pi, int nb, double* lam_u,
+                              double* lamB_extra, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int N = g.nx * g.ny * g.nz;
+  double best = -1.0;
+  int n = -1;
+  for (int b = 0; b < nb; ++b)
+    if (pv[b] > best || (pv[b] == best && pi[b] >= 0 && pi[b] < n)) {
+      best = pv[b];
+      n = pi[b];
+    }
+  out[0] = best;
+  if (n < 0) return;
+  const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+  double G[3][3], P[3][3], cc[3], V[3], J[3], u[3];
+  current_at(g, y, Bb, rb, n, i, j, k, G, P, cc, V, J);
+  const double B[3] = {Bb[n], Bb[N + n], Bb[2 * N + n]};
+  cross3(J, B, u);
+  const double um = sqrt(dot(u, u)), b2 = dot(B, B);
+  for (int c = 0; c < 3; ++c) {
+    lam_u[c * N + n] = um > 0.0 ? u[c] / (um * b2) : 0.0;
+    lamB_extra[c * N + n] = -2.0 * um * B[c] / (b2 * b2);
+  }
+}
+
+__global__ void k_adj_add(int M, const double* a, double* b) {
+  NODE_LOOP(M) b[n] += a[n];
+}
+
+__global__ void k_adj_zero(int M, double* a) {
+  NODE_LOOP(M) a[n] = 0.0;
+}
+
+// mu (adjoint of B0s) -> adjoint of B0: B0s_a = s_a B0_a.
+__global__ void k_adj_mu_out(AdjGeom g, const double* mu, double* mu_B0) {
+  const int N = g.nx * g.ny * g.nz;
+  NODE_LOOP(N) for (int c = 0; c < 3; ++c) mu_B0[c * N + n] += g.s[c] * mu[c * N + n];
+}
+
+// Parameter contraction out[p] = sum_m dB[p][m] mu[m] (fixed-order sums).
+__global__ void k_param_contract(long long M, const double* dB, const double* mu,
+                                 double* out) {
+  const int p = blockIdx.x;
+  double s = 0.0;
+  for (long long m = threadIdx.x; m < M; m += blockDim.x) s += dB[p * M + m] * mu[m];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[p] = sh[0];
+}
+
+}  // namespace glemur
+
+// ------------------------------------------------------------ host side
+
+namespace glemur {
+// Provided by glemur.cu.
+int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6);
+int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precision,
+             void** d_cur, void** B0s, void** k, void** stream);
+}  // namespace glemur
+
+using namespace glemur;
+
+namespace {
+
+size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Adjoint workspace: k6 (storage type), FP64 stage input, B, 1/det, six
+// stage adjoints, the stage-input adjoint, the P and g adjoints, the
+// 1/det, centre-B, extra-B and velocity adjoints, mu (adjoint of B0s), the
+// xi partials and two small pointer tables.
+struct AdjLayout {
+  size_t k6, y, Bb, rb, lamk, lamy, lamP, lamg, lamr, lamB, lamB2, lamu, mu, pv, pi, ptr,
+      total, fstride;
+};
+
+constexpr int kXiBlocks = 1024;
+
+AdjLayout adj_layout(int nx, int ny, int nz, int precision) {
+  const size_t N = (size_t)nx * ny * nz;
+  const size_t es = precision == GLEMUR_MIXED ? 4 : 8;
+  AdjLayout L{};
+  size_t o = 0;
+  L.fstride = al(3 * N * 8);
+  L.k6 = o; o += al(3 * N * es);
+  L.y = o; o += L.fstride;
+  L.Bb = o; o += L.fstride;
+  L.rb = o; o += al(N * 8);
+  L.lamk = o; o += 6 * L.fstride;
+  L.lamy = o; o += L.fstride;
+  L.lamP = o; o += al(9 * N * 8);
+  L.lamg = o; o += al(9 * N * 8);
+  L.lamr = o; o += al(N * 8);
+  L.lamB = o; o += L.fstride;
+  L.lamB2 = o; o += L.fstride;
+  L.lamu = o; o += L.fstride;
+  L.mu = o; o += L.fstride;
+  L.pv = o; o += al(kXiBlocks * 8 + 8);
+  L.pi = o; o += al(kXiBlocks * 4);
+  L.ptr = o; o += 256;
+  L.total = o;
+  return L;
+}
+
+struct Adj {
+  int N, precision;
+  AdjGeom g;
+  void* d;
+  void* B0s;
+  void* k[5];
+  cudaStream_t s;
+  unsigned char* ws;
+  AdjLayout L;
+  double* P(size_t off) const { return (double*)(ws + off); }
+};
+
+int adj_open(glemur_ctx* c, void* ws, size_t bytes, Adj* A) {
+  if (!c || !ws || ((uintptr_t)ws & 255)) return GLEMUR_ERR_BADARG;
+  double h[3];
+  void* stream = nullptr;
+  int nx, ny, nz;
+  int rc = ctx_info(c, &nx, &ny, &nz, h, &A->precision, &A->d, &A->B0s, A->k, &stream);
+  if (rc) return rc;
+  A->s = (cudaStream_t)stream;
+  A->N = nx * ny * nz;
+  A->L = adj_layout(nx, ny, nz, A->precision);
+  if (bytes < A->L.total) return GLEMUR_ERR_WORKSPACE;
+  A->ws = (unsigned char*)ws;
+  A->g.nx = nx;
+  A->g.ny = ny;
+  A->g.nz = nz;
+  for (int a = 0; a < 3; ++a) A->g.h2[a] = 2.0 * h[a];
+  A->g.s[0] = 4.0 * h[1] * h[2];
+  A->g.s[1] = 4.0 * h[2] * h[0];
+  A->g.s[2] = 4.0 * h[0] * h[1];
+  return GLEMUR_OK;
+}
+
+int nblk(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
+}
+
+// The stage VJP at the stage input already in y: lam_u -> lam_y, mu +=.
+template <typename T>
+void stage_vjp(const Adj& A, const double* lam_u, const double* extra_lamB, double wE) {
+  const int N = A.N;
+  double* y = A.P(A.L.y);
+  double* Bb = A.P(A.L.Bb);
+  double* rb = A.P(A.L.rb);
+  k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, Bb, rb);
+  if (lam_u) {
+    k_adj_current<<<nblk(N), 256, 0, A.s>>>(A.g, y, Bb, rb, lam_u, A.P(A.L.lamP), A.P(A.L.lamg),
+                                            A.P(A.L.lamr), A.P(A.L.lamB));
+  } else {
+    k_adj_zero<<<nblk(9 * N), 256, 0, A.s>>>(9 * N, A.P(A.L.lamP));
+    k_adj_zero<<<nblk(9 * N), 256, 0, A.s>>>(9 * N, A.P(A.L.lamg));
+    k_adj_zero<<<nblk(N), 256, 0, A.s>>>(N, A.P(A.L.lamr));
+    k_adj_zero<<<nblk(3 * N), 256, 0, A.s>>>(3 * N, A.P(A.L.lamB));
+  }
+  if (extra_lamB) k_adj_add<<<nblk(3 * N), 256, 0, A.s>>>(3 * N, extra_lamB, A.P(A.L.lamB));
+  k_adj_pullback<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, rb, A.P(A.L.lamP),
+                                               A.P(A.L.lamg), A.P(A.L.lamr), A.P(A.L.lamB), wE,
+                                               A.P(A.L.mu));
+  k_adj_positions<<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.lamg), A.P(A.L.lamy));
+}
+
+template <typename T>
+int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, double* lam,
+               double* mu_B0) {
+  const int N3 = 3 * A.N;
+  int rc = ctx_recompute_stages(c, dt, A.ws + A.L.k6);
+  if (rc) return rc;
+  double* lamk_h[6];
+  for (int j = 0; j < 6; ++j) lamk_h[j] = A.P(A.L.lamk + j * A.L.fstride);
+  const T* kp[6] = {(const T*)A.k[0], (const T*)A.k[1], (const T*)A.k[2], (const T*)A.k[3],
+                    (const T*)A.k[4], (const T*)(A.ws + A.L.k6)};
+  double** lamk_d = (double**)(A.ws + A.L.ptr);
+  const T** kp_d = (const T**)(A.ws + A.L.ptr + 64);
+  cudaError_t e = cudaMemcpyAsync(lamk_d, lamk_h, sizeof(lamk_h), cudaMemcpyHostToDevice, A.s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(kp_d, kp, sizeof(kp), cudaMemcpyHostToDevice, A.s);
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.mu));
+  k_adj_seed<<<nblk(N3), 256, 0, A.s>>>(N3, lam_next, dt, lam, lamk_d);
+  for (int s = 5; s >= 0; --s) {
+    k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, s, dt, A.P(A.L.y));
+    stage_vjp<T>(A, lamk_h[s], nullptr, 0.0);
+    k_adj_rk<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamy), s, dt, lam, lamk_d);
+  }
+  k_adj_mu_out<<<nblk(A.N), 256, 0, A.s>>>(A.g, A.P(A.L.mu), mu_B0);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(A.s);  // pointer tables are host stack
+  return e == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA;
+}
+
+template <typename T>
+int loss_grad_t(glemur_ctx* c, const Adj& A, int loss, double* value, double* lam,
+                double* mu_B0) {
+  const int N = A.N, N3 = 3 * N;
+  const T* kp[1] = {nullptr};
+  const T** kp_d = (const T**)(A.ws + A.L.ptr + 64);
+  if (cudaMemcpyAsync(kp_d, kp, sizeof(kp), cudaMemcpyHostToDevice, A.s)) return GLEMUR_ERR_CUDA;
+  k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.mu));
+  k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, 0, 0.0, A.P(A.L.y));
+  double v = 0.0;
+  if (loss == 0) {
+    stage_vjp<T>(A, nullptr, nullptr, 1.0);
+    int rc = glemur_energy(c, &v);
+    if (rc) return rc;
+  } else {
+    double* Bb = A.P(A.L.Bb);
+    double* rb = A.P(A.L.rb);
+    k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.y), (const T*)A.B0s, Bb, rb);
+    const int nb = nblk(N) < kXiBlocks ? nblk(N) : kXiBlocks;
+    double* pv = A.P(A.L.pv);
+    int* pi = (int*)(A.ws + A.L.pi);
+    k_adj_xi_partial<<<nb, 256, 0, A.s>>>(A.g, A.P(A.L.y), Bb, rb, pv, pi);
+    k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamu));
+    k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamB2));
+    double* out = pv + kXiBlocks;
+    k_adj_xi_seed<<<1, 32, 0, A.s>>>(A.g, A.P(A.L.y), Bb, rb, pv, pi, nb, A.P(A.L.lamu),
+                                     A.P(A.L.lamB2), out);
+    stage_vjp<T>(A, A.P(A.L.lamu), A.P(A.L.lamB2), 0.0);
+    if (cudaMemcpyAsync(&v, out, sizeof(double), cudaMemcpyDeviceToHost, A.s))
+      return GLEMUR_ERR_CUDA;
+  }
+  cudaMemcpyAsync(lam, A.P(A.L.lamy), sizeof(double) * N3, cudaMemcpyDeviceToDevice, A.s);
+  k_adj_mu_out<<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.mu), mu_B0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(A.s);
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  if (value) *value = v;
+  return GLEMUR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t glemur_adjoint_workspace_bytes(int nx, int ny, int nz, int precision) {
+  if (nx < 3 || ny < 3 || nz < 3 || 9LL * nx * ny * nz >= (1LL << 31)) return 0;
+  if (precision != GLEMUR_FP64 && precision != GLEMUR_MIXED) return 0;
+  return adj_layout(nx, ny, nz, precision).total;
+}
+
+int glemur_vjp_step(glemur_ctx* c, double dt, const double* lam_next, double* lam,
+                    double* mu_B0, void* adj_ws, size_t adj_bytes) {
+  if (!lam_next || !lam || !mu_B0 || !(dt > 0) || !std::isfinite(dt)) return GLEMUR_ERR_BADARG;
+  Adj A;
+  int rc = adj_open(c, adj_ws, adj_bytes, &A);
+  if (rc) return rc;
+  return A.precision == GLEMUR_MIXED ? vjp_step_t<float>(c, A, dt, lam_next, lam, mu_B0)
+                                     : vjp_step_t<double>(c, A, dt, lam_next, lam, mu_B0);
+}
+
+int glemur_loss_grad(glemur_ctx* c, int loss, double* value, double* lam, double* mu_B0,
+                     void* adj_ws, size_t adj_bytes) {
+  if (!lam || !mu_B0 || (loss != GLEMUR_LOSS_ENERGY && loss != GLEMUR_LOSS_XI))
+    return GLEMUR_ERR_BADARG;
+  Adj A;
+  int rc = adj_open(c, adj_ws, adj_bytes, &A);
+  if (rc) return rc;
+  return A.precision == GLEMUR_MIXED ? loss_grad_t<float>(c, A, loss, value, lam, mu_B0)
+                                     : loss_grad_t<double>(c, A, loss, value, lam, mu_B0);
+}
+
+int glemur_param_contract(int n_params, long long m, const double* dB0, const double* mu,
+                          double* out, void* stream) {
+  if (n_params < 1 || m < 1 || !dB0 || !mu || !out) return GLEMUR_ERR_BADARG;
+  k_param_contract<<<n_params, 256, 0, (cudaStream_t)stream>>>(m, dB0, mu, out);
+  return cudaGetLastError() == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA;
+}
+
+}  // extern "C"

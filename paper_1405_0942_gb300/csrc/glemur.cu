@@ -59,6 +59,7 @@ __device__ void set_coeffs(DevState* st) {
 __global__ void k_reset_state(DevState* st, double dt0, double lambda0, double dt_min,
                               double grow_max, double shrink_min, int max_rejects) {
   st->dt = dt0;
+  st->dt_last = 0.0;
   st->t = 0.0;
   st->lambda = 0.0;
   st->lambda0 = lambda0;
@@ -196,6 +197,7 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
     dtn = dt * fac;
   }
   if (accept) {
+    st->dt_last = dt;
     st->t += dt;
     st->cur ^= 1;
     st->n_accept++;
@@ -379,6 +381,7 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.d[1] = (const T*)c->dbuf[1];
   a.B0s = (const T*)c->B0s;
   for (int j = 0; j < 5; ++j) a.k[j] = (T*)c->k[j];
+  a.k6 = nullptr;
   a.stage = stage;
   a.diag = diag;
   a.force = force;
@@ -392,10 +395,12 @@ int nblocks_of(const glemur_ctx* c, int curl) {
   return curl == GLEMUR_CURL_DIRECT ? c->nblocks_direct : c->nblocks;
 }
 
-cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force) {
+cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force,
+                         void* k6 = nullptr) {
   const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
   if (c->o.precision == GLEMUR_MIXED) {
     StageArgs<float> a = make_args<float>(c, stage, diag, force);
+    a.k6 = (float*)k6;
     if (curl == GLEMUR_CURL_DIRECT) {
       a.kz = c->kz_direct;
       a.nblocks = c->nblocks_direct;
@@ -404,6 +409,7 @@ cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int
     return launch_f32_mimetic(a, stage, g, c->s);
   }
   StageArgs<double> a = make_args<double>(c, stage, diag, force);
+  a.k6 = (double*)k6;
   if (curl == GLEMUR_CURL_DIRECT) {
     a.kz = c->kz_direct;
     a.nblocks = c->nblocks_direct;
@@ -440,6 +446,7 @@ void fill_stats(const DevState& hs, int curl, glemur_stats* out) {
   out->xi = hs.xi;
   out->xi_sin = hs.xi_sin;
   out->status = hs.status;
+  out->dt_last = hs.dt_last;
 }
 
 int reset_state(glemur_ctx* c) {
@@ -472,6 +479,41 @@ int stage_out(glemur_ctx* c, double* dst, int mem) {
 }
 
 }  // namespace
+
+namespace glemur {
+
+// Stage derivatives k1..k6 of one attempt of size dt at the current state,
+// without advancing it (k6 into `k6`); used by the adjoint's recompute.
+// Leaves dt as the pending step size.
+int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6) {
+  if (c->o.curl != GLEMUR_CURL_MIMETIC) return GLEMUR_ERR_BADARG;
+  k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 0);
+  cudaError_t e = cudaGetLastError();
+  for (int s = 0; s < 6 && e == cudaSuccess; ++s)
+    e = launch_stage(c, GLEMUR_CURL_MIMETIC, s, 0, 1, s == 5 ? k6 : nullptr);
+  return cuda_rc(e);
+}
+
+// Geometry, storage and the current accepted displacement (synchronises).
+int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precision,
+             void** d_cur, void** B0s, void** k, void** stream) {
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  if (hs.status != ST_OK) return hs.status;
+  *nx = c->nx;
+  *ny = c->ny;
+  *nz = c->nz;
+  for (int a = 0; a < 3; ++a) h[a] = c->h[a];
+  *precision = c->o.precision;
+  *d_cur = c->dbuf[hs.cur];
+  *B0s = c->B0s;
+  for (int j = 0; j < 5; ++j) k[j] = c->k[j];
+  *stream = (void*)c->s;
+  return GLEMUR_OK;
+}
+
+}  // namespace glemur
 
 extern "C" {
 
@@ -589,6 +631,28 @@ int glemur_set_x(glemur_ctx* c, const double* x, int mem) {
                                           (double*)c->dbuf[1]);
   rc = cuda_rc(cudaGetLastError());
   if (rc) return rc;
+  return reset_state(c);
+}
+
+size_t glemur_state_bytes(const glemur_ctx* c) {
+  return c ? (size_t)(3 * c->N) * c->esize : 0;
+}
+
+int glemur_get_state(glemur_ctx* c, void* buf) {
+  if (!c || !buf) return GLEMUR_ERR_BADARG;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  return cuda_rc(cudaMemcpyAsync(buf, c->dbuf[hs.cur], glemur_state_bytes(c),
+                                 cudaMemcpyDeviceToDevice, c->s));
+}
+
+int glemur_set_state(glemur_ctx* c, const void* buf) {
+  if (!c || !buf) return GLEMUR_ERR_BADARG;
+  const size_t n = glemur_state_bytes(c);
+  cudaError_t e = cudaMemcpyAsync(c->dbuf[0], buf, n, cudaMemcpyDeviceToDevice, c->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->dbuf[1], buf, n, cudaMemcpyDeviceToDevice, c->s);
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
   return reset_state(c);
 }
 

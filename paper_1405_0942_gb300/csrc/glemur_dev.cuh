@@ -44,6 +44,7 @@ constexpr int ST_DT_UNDERFLOW = -5;
 // to synchronise between attempts.
 struct DevState {
   double dt;          // step size of the next attempt
+  double dt_last;     // step size of the last accepted attempt
   double t;           // time of the accepted state
   double lambda;      // error estimate of the last attempt
   double lambda0, dt_min, grow_max, shrink_min;
@@ -78,6 +79,7 @@ struct StageArgs {
   const T* d[2];       // ping-pong displacement buffers (3N each)
   const T* B0s;        // pre-scaled B0 (3N)
   T* k[5];             // stage derivatives k1..k5 (3N each)
+  T* k6;               // if set, the last stage also stores k6 here
   int stage;           // 0..5 (stage s+1 of Cash-Karp)
   int diag;            // reduce E_M / xi partials in this launch
   int force;           // run even if the step target is reached

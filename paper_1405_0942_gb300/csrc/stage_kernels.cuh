@@ -406,6 +406,7 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, co
       er = fma(e5, u[c], er);
       dout[c * N + n] = (T)((C)__ldg(&d[c * N + n]) + up);
       acc.max_lam(fabs(er));
+      if (a.k6) a.k6[c * N + n] = (T)u[c];
     }
   }
 }

@@ -40,12 +40,13 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("t", C.c_double),
                 ("dt", C.c_double), ("lambda_", C.c_double), ("energy", C.c_double),
-                ("xi", C.c_double), ("xi_sin", C.c_double), ("status", C.c_int)]
+                ("xi", C.c_double), ("xi_sin", C.c_double), ("status", C.c_int),
+                ("dt_last", C.c_double)]
 
     def as_dict(self):
         return dict(accepted=self.accepted, rejected=self.rejected, t=self.t, dt=self.dt,
                     lam=self.lambda_, energy=self.energy, xi=self.xi, xi_sin=self.xi_sin,
-                    status=self.status)
+                    status=self.status, dt_last=self.dt_last)
 
 
 EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
@@ -53,7 +54,10 @@ EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
            "glemur_step", "glemur_attempts", "glemur_step_fixed", "glemur_energy",
            "glemur_forcefree_err", "glemur_get_stats", "glemur_kernels_per_attempt",
            "glemur_profile_attempt", "glemur_energy_static", "glemur_destroy",
-           "glemur_strerror"]
+           "glemur_strerror", "glemur_adjoint_workspace_bytes", "glemur_vjp_step",
+           "glemur_loss_grad", "glemur_param_contract", "glemur_state_bytes",
+           "glemur_get_state", "glemur_set_state"]
+LOSS_ENERGY, LOSS_XI = 0, 1
 
 _lib = None
 
@@ -94,6 +98,15 @@ def lib() -> C.CDLL:
     L.glemur_kernels_per_attempt.argtypes = [vp]
     L.glemur_profile_attempt.argtypes = [vp, C.POINTER(C.c_float), ip]
     L.glemur_energy_static.argtypes = [ip, ip, ip, dp, dp, vp, vp, vp, vp]
+    L.glemur_adjoint_workspace_bytes.argtypes = [ip, ip, ip, ip]
+    L.glemur_adjoint_workspace_bytes.restype = C.c_size_t
+    L.glemur_vjp_step.argtypes = [vp, C.c_double, vp, vp, vp, vp, C.c_size_t]
+    L.glemur_loss_grad.argtypes = [vp, ip, dp, vp, vp, vp, C.c_size_t]
+    L.glemur_param_contract.argtypes = [ip, C.c_longlong, vp, vp, vp, vp]
+    L.glemur_state_bytes.argtypes = [vp]
+    L.glemur_state_bytes.restype = C.c_size_t
+    L.glemur_get_state.argtypes = [vp, vp]
+    L.glemur_set_state.argtypes = [vp, vp]
     L.glemur_destroy.argtypes = [vp]
     L.glemur_destroy.restype = None
     L.glemur_strerror.argtypes = [ip]
@@ -258,3 +271,145 @@ class Relaxation:
         if n < 0:
             raise GlemurError(n, "glemur_profile_attempt")
         return [ms[i] for i in range(n)]
+
+    # -- exact checkpoints ------------------------------------------------
+    def get_state(self, out=None):
+        """Raw state (displacement in storage precision) as a uint8 CUDA
+        tensor: an exact checkpoint."""
+        import torch
+        n = int(lib().glemur_state_bytes(self._h))
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=self.device)
+        _check(lib().glemur_get_state(self._h, C.c_void_p(out.data_ptr())), "glemur_get_state")
+        return out
+
+    def set_state(self, buf):
+        _check(lib().glemur_set_state(self._h, C.c_void_p(buf.data_ptr())), "glemur_set_state")
+
+    # -- adjoint ----------------------------------------------------------
+    def _adj_ws(self):
+        import torch
+        ws = getattr(self, "_adjoint_ws", None)
+        if ws is None:
+            nx, ny, nz = self.dims
+            n = int(lib().glemur_adjoint_workspace_bytes(nx, ny, nz, self.opts.precision))
+            if n == 0:
+                raise GlemurError(-1, "glemur_adjoint_workspace_bytes")
+            ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+            self._adjoint_ws = ws
+        return ws
+
+    def vjp_step(self, dt, lam_next, lam, mu_B0):
+        """lam = (dx_{n+1}/dx_n)^T lam_next, mu_B0 += (dx_{n+1}/dB0)^T lam_next
+        for one step of size dt from the current state (CUDA float64 fields)."""
+        ws = self._adj_ws()
+        for t in (lam_next, lam, mu_B0):
+            _field_ptr(t, self.shape, writable=True)
+        _check(lib().glemur_vjp_step(self._h, float(dt), C.c_void_p(lam_next.data_ptr()),
+                                     C.c_void_p(lam.data_ptr()), C.c_void_p(mu_B0.data_ptr()),
+                                     C.c_void_p(ws.data_ptr()), ws.numel()), "glemur_vjp_step")
+
+    def loss_grad(self, loss, lam, mu_B0):
+        """Loss of the current state; its position gradient into lam and its
+        B0 gradient added to mu_B0."""
+        ws = self._adj_ws()
+        v = C.c_double()
+        _check(lib().glemur_loss_grad(self._h, int(loss), C.byref(v), C.c_void_p(lam.data_ptr()),
+                                      C.c_void_p(mu_B0.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                      ws.numel()), "glemur_loss_grad")
+        return v.value
+
+
+def param_contract(dB0, mu):
+    """sum over nodes of dB0[p] . mu for each parameter p (CUDA tensors:
+    dB0 (P, 3, nz, ny, nx), mu (3, nz, ny, nx)); returns a (P,) tensor."""
+    import torch
+    P = dB0.shape[0]
+    dB0 = dB0.contiguous()
+    mu = mu.contiguous()
+    out = torch.empty(P, dtype=torch.float64, device=mu.device)
+    _check(lib().glemur_param_contract(P, mu.numel(), C.c_void_p(dB0.data_ptr()),
+                                       C.c_void_p(mu.data_ptr()), C.c_void_p(out.data_ptr()),
+                                       C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "glemur_param_contract")
+    return out
+
+
+def relax_with_schedule(relax, x0, n_steps):
+    """Run n_steps error-controlled steps from x0 and return the accepted
+    step sizes (the schedule the adjoint replays)."""
+    relax.set_x(x0)
+    dts = []
+    for _ in range(n_steps):
+        st = relax.step(1)
+        dts.append(st["dt_last"])
+    return dts
+
+
+def loss_and_field_gradient(relax, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+    """Loss of the state reached from x0 by the step-size schedule `dts`
+    (replayed exactly: the control law is piecewise constant in the inputs)
+    and its gradient with respect to the relaxation's B0.
+
+    Memory: positions are kept every `checkpoint_every` steps; the backward
+    pass recomputes each segment forwards, storing its states, then runs the
+    steps' vector-Jacobian products in reverse (glemur_vjp_step).
+    """
+    import torch
+    n = len(dts)
+    every = max(1, int(checkpoint_every))
+    relax.set_x(x0)
+    ckpts = [relax.get_state()]
+    for i, dt in enumerate(dts):
+        relax.step_fixed(dt)
+        if (i + 1) % every == 0 and i + 1 < n:
+            ckpts.append(relax.get_state())
+    lam = torch.zeros(relax.shape, dtype=torch.float64, device=relax.device)
+    lam_next = torch.zeros_like(lam)
+    mu = torch.zeros_like(lam)
+    value = None
+    nseg = (n + every - 1) // every if n > 0 else 0
+    if n == 0:
+        relax.set_x(x0)
+        value = relax.loss_grad(loss, lam, mu)
+        return value, mu, lam
+    for c in reversed(range(nseg)):
+        start, end = c * every, min((c + 1) * every, n)
+        relax.set_state(ckpts[c])
+        states = [ckpts[c]]
+        for i in range(start, end):
+            relax.step_fixed(dts[i])
+            states.append(relax.get_state())
+        if value is None:
+            relax.set_state(states[-1])
+            value = relax.loss_grad(loss, lam_next, mu)
+        for i in reversed(range(start, end)):
+            relax.set_state(states[i - start])
+            relax.vjp_step(dts[i], lam_next, lam, mu)
+            lam_next, lam = lam, lam_next
+        del states
+    return value, mu, lam_next
+
+
+class RelaxationLoss:
+    """torch.autograd.Function factory: loss(B0) of the relaxed state, with
+    the hand-written adjoint as its backward."""
+
+    @staticmethod
+    def apply(relax, B0, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, B0_):
+                relax.set_B0(B0_.detach())
+                value, mu, _ = loss_and_field_gradient(relax, x0, dts, loss, checkpoint_every)
+                ctx.save_for_backward(mu)
+                return torch.tensor(value, dtype=torch.float64, device=B0_.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                (mu,) = ctx.saved_tensors
+                return g * mu
+
+        return _Fn.apply(B0)
