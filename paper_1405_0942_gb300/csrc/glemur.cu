@@ -26,6 +26,22 @@ int ctas_per_sm_f64_direct();
 int ctas_per_sm_f32_mimetic();
 int ctas_per_sm_f32_direct();
 
+struct SplitArgs {
+  int nx, ny, nz;
+  double h2[3];
+  const double* d[2];
+  const double* B0s;
+  double* k[6];
+  double* ys[2];
+  double* Bb;
+  double* rb;
+  int diag, force;
+  DevState* st;
+  double* part;
+  int nblocks;
+};
+cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s);
+
 // Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
 // of section "Time Stepping".
 __constant__ double CK_A[6][6] = {
@@ -287,6 +303,10 @@ struct glemur_ctx {
   double* stage;    // 3N doubles for host transfers
   double* part;     // NPART * max_blocks
   DevState* st;
+  int split;                             // FP64 mimetic stages in two passes
+  double* ys[2];                         // split path: stage inputs
+  double* Bb;                            // split path: B
+  double* rb;                            // split path: 1/det G
   int max_blocks, nblocks, kz;          // mimetic-current launches
   int nblocks_direct, kz_direct;         // direct-current launches
   dim3 grid, grid_direct;
@@ -298,7 +318,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field, stage, part, state, ptrs, total;
+  size_t field, stage, part, state, ptrs, split, total;
   int max_blocks;
 };
 
@@ -318,7 +338,11 @@ Layout layout(int nx, int ny, int nz, int precision) {
   L.part = align256((size_t)NPART * L.max_blocks * sizeof(double));
   L.state = align256(sizeof(DevState));
   L.ptrs = 256;
-  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs;
+  // FP64: two stage inputs, B and 1/det G for the two-pass stages
+  L.split = precision == GLEMUR_FP64 ? 3 * align256((size_t)(3 * N) * 8) +
+                                           align256((size_t)N * 8)
+                                     : 0;
+  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.split;
   return L;
 }
 
@@ -395,8 +419,32 @@ int nblocks_of(const glemur_ctx* c, int curl) {
   return curl == GLEMUR_CURL_DIRECT ? c->nblocks_direct : c->nblocks;
 }
 
+cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, void* k6) {
+  SplitArgs a;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  for (int i = 0; i < 3; ++i) a.h2[i] = 2.0 * c->h[i];
+  a.d[0] = (const double*)c->dbuf[0];
+  a.d[1] = (const double*)c->dbuf[1];
+  a.B0s = (const double*)c->B0s;
+  for (int j = 0; j < 5; ++j) a.k[j] = (double*)c->k[j];
+  a.k[5] = (double*)k6;
+  a.ys[0] = c->ys[0];
+  a.ys[1] = c->ys[1];
+  a.Bb = c->Bb;
+  a.rb = c->rb;
+  a.diag = diag;
+  a.force = force;
+  a.st = c->st;
+  a.part = c->part;
+  a.nblocks = c->nblocks;
+  return launch_f64_split(a, stage, c->s);
+}
+
 cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force,
                          void* k6 = nullptr) {
+  if (c->split && curl == GLEMUR_CURL_MIMETIC) return launch_split(c, stage, diag, force, k6);
   const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
   if (c->o.precision == GLEMUR_MIXED) {
     StageArgs<float> a = make_args<float>(c, stage, diag, force);
@@ -447,6 +495,16 @@ void fill_stats(const DevState& hs, int curl, glemur_stats* out) {
   out->xi_sin = hs.xi_sin;
   out->status = hs.status;
   out->dt_last = hs.dt_last;
+}
+
+// The two-pass FP64 stages write stage inputs at interior nodes only; the
+// boundary entries must hold the (fixed) boundary positions.
+int seed_stage_inputs(glemur_ctx* c) {
+  if (!c->ys[0]) return GLEMUR_OK;
+  const size_t n = sizeof(double) * 3 * c->N;
+  cudaError_t e = cudaMemcpyAsync(c->ys[0], c->dbuf[0], n, cudaMemcpyDeviceToDevice, c->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->ys[1], c->dbuf[0], n, cudaMemcpyDeviceToDevice, c->s);
+  return cuda_rc(e);
 }
 
 int reset_state(glemur_ctx* c) {
@@ -580,8 +638,19 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->stage = (double*)p; p += L.stage;
   c->part = (double*)p; p += L.part;
   c->st = (DevState*)p; p += L.state;
-  c->dbuf_dev = (void**)p;
+  c->dbuf_dev = (void**)p; p += L.ptrs;
   c->max_blocks = L.max_blocks;
+  c->split = 0;
+  c->ys[0] = c->ys[1] = c->Bb = c->rb = nullptr;
+  if (L.split) {
+    const size_t f8 = align256((size_t)(3 * c->N) * 8);
+    c->ys[0] = (double*)p; p += f8;
+    c->ys[1] = (double*)p; p += f8;
+    c->Bb = (double*)p; p += f8;
+    c->rb = (double*)p;
+    const char* fused = getenv("GLEMUR_F64_FUSED");
+    c->split = !(fused && atoi(fused) > 0);
+  }
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -599,6 +668,12 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->kz = choose_kz(nz, gx * gy, c->nsm, pm, !mixed);
   c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
   c->nblocks = gx * gy * (int)c->grid.z;
+  if (c->split) {
+    // grid-stride passes: up to 4 CTAs of 256 threads per SM
+    const long long need = (c->N + 255) / 256;
+    const long long cap = 4LL * c->nsm;
+    c->nblocks = (int)(need < cap ? need : cap);
+  }
   c->kz_direct = choose_kz(nz, gx * gy, c->nsm, pd, !mixed);
   c->grid_direct = dim3(gx, gy, (nz + c->kz_direct - 1) / c->kz_direct);
   c->nblocks_direct = gx * gy * (int)c->grid_direct.z;
@@ -609,6 +684,7 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   void* ptrs[2] = {c->dbuf[0], c->dbuf[1]};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->dbuf_dev, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, c->s);
+  if (e == cudaSuccess) e = seed_stage_inputs(c) == GLEMUR_OK ? cudaSuccess : cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
   if (e != cudaSuccess || reset_state(c) != GLEMUR_OK) {
     delete c;
@@ -631,6 +707,7 @@ int glemur_set_x(glemur_ctx* c, const double* x, int mem) {
                                           (double*)c->dbuf[1]);
   rc = cuda_rc(cudaGetLastError());
   if (rc) return rc;
+  if ((rc = seed_stage_inputs(c))) return rc;
   return reset_state(c);
 }
 
@@ -653,6 +730,8 @@ int glemur_set_state(glemur_ctx* c, const void* buf) {
   cudaError_t e = cudaMemcpyAsync(c->dbuf[0], buf, n, cudaMemcpyDeviceToDevice, c->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->dbuf[1], buf, n, cudaMemcpyDeviceToDevice, c->s);
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  int rc = seed_stage_inputs(c);
+  if (rc) return rc;
   return reset_state(c);
 }
 
@@ -786,15 +865,16 @@ int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
   return GLEMUR_OK;
 }
 
-int glemur_kernels_per_attempt(const glemur_ctx* c) { return c ? 7 : 0; }
+int glemur_kernels_per_attempt(const glemur_ctx* c) {
+  return c ? (c->split && c->o.curl == GLEMUR_CURL_MIMETIC ? 13 : 7) : 0;
+}
 
 int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
-  const int nk = glemur_kernels_per_attempt(c);
-  if (!c || !ms || cap < nk) return GLEMUR_ERR_BADARG;
+  if (!c || !ms || cap < 7) return GLEMUR_ERR_BADARG;
   cudaEvent_t ev[8];
   int made = 0;
   cudaError_t e = cudaSuccess;
-  for (; made < nk + 1 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  for (; made < 8 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
   if (e != cudaSuccess) {
     for (int i = 0; i < made - 1; ++i) cudaEventDestroy(ev[i]);
     return GLEMUR_ERR_CUDA;
@@ -813,9 +893,9 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->s);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
-  for (int i = 0; i < nk && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
-  for (int i = 0; i < nk + 1; ++i) cudaEventDestroy(ev[i]);
-  return e == cudaSuccess ? nk : GLEMUR_ERR_CUDA;
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+  return e == cudaSuccess ? 7 : GLEMUR_ERR_CUDA;
 }
 
 void glemur_destroy(glemur_ctx* c) { delete c; }

@@ -1,0 +1,236 @@
+// FP64 stage evaluation in two passes, without halo recomputation.
+//
+// On GB300 the FP64 pipe (2 lanes per SM per cycle, 1/64 of FP32) bounds
+// the FP64 step, not HBM.  The fused stage kernel recomputes B on the tile
+// halo (about 1.7 B evaluations per node) and the stage input on the
+// halo-2 tile (about 2.5 combines per node); for FP64 those FP64
+// instructions cost more than the extra HBM traffic of writing B once.  So
+// the FP64 path evaluates each stage as
+//   pass B:  B = G B0s / det G and 1/det G at every node, from the stage
+//            input y_s (index-space differences: central inside,
+//            second-order one-sided on boundary faces; eq. "B
+//            transformation");
+//   pass C:  the mimetic current J = (c_0 g_0 + c_1 g_1 + c_2 g_2)/det G
+//            and u = J x B at interior nodes (eqs. "current discrete" to
+//            "current matrix equation", eq. "magneto friction"), writing
+//            k_s and, pointwise, the next stage input
+//            y_{s+1} = d + sum_{j<=s} dt a_{s+1,j} k_j; the last stage
+//            writes the fifth-order update and the embedded error instead.
+// Both are grid-stride kernels over a fixed number of CTAs, so every SM is
+// busy; the per-CTA partials (Lambda, E_M, xi) keep the fused kernel's
+// layout.
+#include "stage_kernels.cuh"
+
+namespace glemur {
+
+struct SplitArgs {
+  int nx, ny, nz;
+  double h2[3];
+  const double* d[2];  // ping-pong displacements
+  const double* B0s;
+  double* k[6];        // k1..k5 (k[5] = optional k6)
+  double* ys[2];       // stage inputs: y_s in ys[s & 1] (s >= 1), 3N each;
+                       // boundary entries hold the fixed boundary positions
+  double* Bb;          // B, 3N
+  double* rb;          // 1/det G, N
+  int diag, force;
+  DevState* st;
+  double* part;
+  int nblocks;
+};
+
+__device__ __forceinline__ void split_nodes(const SplitArgs& a, int n, int& i, int& j, int& k) {
+  i = n % a.nx;
+  const int r = n / a.nx;
+  j = r % a.ny;
+  k = r / a.ny;
+}
+
+// Column a of G at node (i, j, k) from the stage input y.
+__device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __restrict__ y, int N,
+                                           int n, int ax, int idx, int ext, int stride,
+                                           double out[3]) {
+  const int kind = idx == 0 ? 1 : (idx == ext - 1 ? 2 : 0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double* v = y + c * N;
+    double d;
+    if (kind == 0)
+      d = __ldg(&v[n + stride]) - __ldg(&v[n - stride]);
+    else if (kind == 1)
+      d = (4.0 * __ldg(&v[n + stride]) - 3.0 * __ldg(&v[n])) - __ldg(&v[n + 2 * stride]);
+    else
+      d = (3.0 * __ldg(&v[n]) - 4.0 * __ldg(&v[n - stride])) + __ldg(&v[n - 2 * stride]);
+    out[c] = d;
+  }
+  out[ax] += a.h2[ax];
+}
+
+// Pass B (stage s): B and 1/det G at every node; in the diagnostic launch
+// also the energy partials (eq. "magnetic energy").
+template <int S>
+__global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  __shared__ double red[8];
+  const int N = a.nx * a.ny * a.nz;
+  const double* y = S == 0 ? a.d[st->cur] : a.ys[S & 1];
+  double eacc = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    int i, j, k;
+    split_nodes(a, n, i, j, k);
+    double g0[3], g1[3], g2[3];
+    split_gcol(a, y, N, n, 0, i, a.nx, 1, g0);
+    split_gcol(a, y, N, n, 1, j, a.ny, a.nx, g1);
+    split_gcol(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
+    const double det = det3(g0, g1, g2);
+    if (det <= 0.0)  // NaN: reported by the error norm
+      atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+    const double r = 1.0 / det;
+    const double b0 = __ldg(&a.B0s[n]), b1 = __ldg(&a.B0s[N + n]), b2 = __ldg(&a.B0s[2 * N + n]);
+    double B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      B[c] = (g0[c] * b0 + g1[c] * b1 + g2[c] * b2) * r;
+      a.Bb[c * N + n] = B[c];
+    }
+    a.rb[n] = r;
+    if (S == 0 && a.diag) {
+      const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) +
+                     (k == 0 || k == a.nz - 1);
+      const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
+      eacc += zeta * dot3(B, B) * det;
+    }
+  }
+  if (S == 0 && a.diag) {
+    const int bid = blockIdx.x;
+    const double v = block_reduce<false>(eacc, red);
+    if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
+  }
+}
+
+// Pass C (stage s): current and velocity at interior nodes; k_s and the
+// next stage input, or (s = 5) the update, the error and k6.
+template <int S>
+__global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
+  constexpr bool FINAL = S == 5;
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  __shared__ double red[8];
+  const int N = a.nx * a.ny * a.nz;
+  const int cur = st->cur;
+  const double* d = a.d[cur];
+  double* dout = const_cast<double*>(a.d[cur ^ 1]);
+  const double* y = S == 0 ? d : a.ys[S & 1];
+  double* ynext = a.ys[(S + 1) & 1];
+  double an[5];  // dt a_{S+1, j}: next stage input (non-final stages)
+#pragma unroll
+  for (int j = 0; j < 5; ++j) an[j] = (!FINAL && j <= S) ? st->dta[S + 1][j] : 0.0;
+  Acc<double> acc;
+  const int sy = a.nx, sz = a.nx * a.ny;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    int i, j, k;
+    split_nodes(a, n, i, j, k);
+    if (i < 1 || i > a.nx - 2 || j < 1 || j > a.ny - 2 || k < 1 || k > a.nz - 2) continue;
+    double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double* v = y + c * N;
+      const double* b = a.Bb + c * N;
+      g0[c] = __ldg(&v[n + 1]) - __ldg(&v[n - 1]);
+      g1[c] = __ldg(&v[n + sy]) - __ldg(&v[n - sy]);
+      g2[c] = __ldg(&v[n + sz]) - __ldg(&v[n - sz]);
+      P0[c] = __ldg(&b[n + 1]) - __ldg(&b[n - 1]);
+      P1[c] = __ldg(&b[n + sy]) - __ldg(&b[n - sy]);
+      P2[c] = __ldg(&b[n + sz]) - __ldg(&b[n - sz]);
+      B[c] = __ldg(&b[n]);
+    }
+    g0[0] += a.h2[0];
+    g1[1] += a.h2[1];
+    g2[2] += a.h2[2];
+    const double c0 = dot3(P1, g2) - dot3(P2, g1);
+    const double c1 = dot3(P2, g0) - dot3(P0, g2);
+    const double c2 = dot3(P0, g1) - dot3(P1, g0);
+    const double r = __ldg(&a.rb[n]);
+    double J[3], u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
+    u[0] = J[1] * B[2] - J[2] * B[1];
+    u[1] = J[2] * B[0] - J[0] * B[2];
+    u[2] = J[0] * B[1] - J[1] * B[0];
+    if (S == 0 && a.diag) {
+      const double u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
+      if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
+      const double jb = j2 * b2;
+      if (jb > 0.0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+    }
+    if (!FINAL) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a.k[S][c * N + n] = u[c];
+        // next stage input y_{S+1} = d + sum_{j<=S} dt a_{S+1,j} k_j
+        double v = __ldg(&d[c * N + n]);
+#pragma unroll
+        for (int jj = 0; jj < S; ++jj) v = fma(an[jj], __ldg(&a.k[jj][c * N + n]), v);
+        v = fma(an[S], u[c], v);
+        ynext[c * N + n] = v;
+      }
+    } else {
+      const double b0 = st->dtb[0], b2 = st->dtb[2], b3 = st->dtb[3], b5 = st->dtb[5];
+      const double e0 = st->dte[0], e2 = st->dte[2], e3 = st->dte[3], e4 = st->dte[4],
+                   e5 = st->dte[5];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double k1 = __ldg(&a.k[0][c * N + n]), k3 = __ldg(&a.k[2][c * N + n]),
+                     k4 = __ldg(&a.k[3][c * N + n]), k5 = __ldg(&a.k[4][c * N + n]);
+        double up = b0 * k1;
+        up = fma(b2, k3, up);
+        up = fma(b3, k4, up);
+        up = fma(b5, u[c], up);
+        double er = e0 * k1;
+        er = fma(e2, k3, er);
+        er = fma(e3, k4, er);
+        er = fma(e4, k5, er);
+        er = fma(e5, u[c], er);
+        dout[c * N + n] = __ldg(&d[c * N + n]) + up;
+        acc.max_lam(fabs(er));
+        if (a.k[5]) a.k[5][c * N + n] = u[c];
+      }
+    }
+  }
+  const int bid = blockIdx.x;
+  if (FINAL) {
+    const double v = block_reduce<true>(acc.lam, red);
+    if (threadIdx.x == 0) a.part[PART_LAMBDA * a.nblocks + bid] = v;
+  }
+  if (S == 0 && a.diag) {
+    double v = block_reduce<true>(acc.xi2, red);
+    if (threadIdx.x == 0) a.part[PART_XI2 * a.nblocks + bid] = v;
+    v = block_reduce<true>(acc.xis2, red);
+    if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
+  }
+}
+
+// Launch both passes of stage s on `nblocks` CTAs of 256 threads.
+cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s) {
+  const dim3 g(a.nblocks);
+#define GLEMUR_SPLIT_CASE(SS)                        \
+  case SS:                                           \
+    k_split_B<SS><<<g, 256, 0, s>>>(a);              \
+    k_split_C<SS><<<g, 256, 0, s>>>(a);              \
+    break;
+  switch (stage) {
+    GLEMUR_SPLIT_CASE(0)
+    GLEMUR_SPLIT_CASE(1)
+    GLEMUR_SPLIT_CASE(2)
+    GLEMUR_SPLIT_CASE(3)
+    GLEMUR_SPLIT_CASE(4)
+    GLEMUR_SPLIT_CASE(5)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef GLEMUR_SPLIT_CASE
+  return cudaGetLastError();
+}
+
+}  // namespace glemur
