@@ -118,6 +118,20 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(seconds, units, world, device):
+    """Whole-job timing over torch.distributed ranks: the slowest rank's
+    time and the units of all ranks (each rank relaxes its own replica)."""
+    if world == 1:
+        return float(seconds), int(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
+
+
 def workload(name, n=None):
     base, nn, _ = gi.WORKLOADS[name]
     return gi.make_workload(base, n=n or nn)
@@ -270,12 +284,9 @@ def our_arm(args):
     r, ms, st = time_mode(G, torch, w, args.precision, args.curl, args.steps, args.warmup, flush)
     barrier()
     clocks = sampler.stop()
-    total_s = ms.sum() * 1e-3                       # device time of the K timed steps
-    if ws > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    units = w.grid.n_interior * 6 * args.steps * ws
+    # device time of the K timed steps; slowest rank, units of all ranks
+    total_s, units = reduce_over_ranks(ms.sum() * 1e-3, w.grid.n_interior * 6 * args.steps,
+                                       ws, "cuda")
     value = units / total_s
     roof = roofline_entry(ms, w, args.precision, args.curl, hbm_peak, peak_kind)
     per_kernel = ms.mean(axis=0).tolist()

@@ -88,6 +88,11 @@ typedef struct {
   int max_rejects;    /* consecutive rejections allowed, 64 */
   int diag_each_attempt; /* 1: every attempt also reduces E_M and xi of the
                             state it starts from (default 1) */
+  double safety;      /* factor s on the adjusted step: s dt (Lambda_0/
+                         Lambda)^0.2 when rejecting or growing; 1 (default)
+                         is the law as printed.  s < 1 (0.9 in Numerical
+                         Recipes' stepper) ends rejection streaks when the
+                         error falls more slowly than dt^5 */
 } glemur_opts;
 
 typedef struct {

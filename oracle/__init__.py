@@ -31,7 +31,7 @@ class _Grid(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("dt_min", C.c_double),
                 ("grow_max", C.c_double), ("shrink_min", C.c_double),
-                ("max_rejects", C.c_int)]
+                ("max_rejects", C.c_int), ("safety", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -51,10 +51,11 @@ class ControlOpts:
     grow_max: float = 5.0
     shrink_min: float = 0.1
     max_rejects: int = 64
+    safety: float = 1.0
 
     def _c(self):
         return _Opts(self.lambda0, self.dt_min, self.grow_max, self.shrink_min,
-                     self.max_rejects)
+                     self.max_rejects, self.safety)
 
 
 _lib = None

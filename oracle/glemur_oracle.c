@@ -575,7 +575,7 @@ int ora_step_control(const ora_control_opts* o, double lambda, double dt,
     return ORA_ERR_NONFINITE;
   }
   if (lambda > o->lambda0) {
-    double fac = pow(o->lambda0 / lambda, 0.2);
+    double fac = o->safety * pow(o->lambda0 / lambda, 0.2);
     if (fac < o->shrink_min) fac = o->shrink_min;
     *accept = 0;
     *dt_next = dt * fac;
@@ -586,7 +586,7 @@ int ora_step_control(const ora_control_opts* o, double lambda, double dt,
   *accept = 1;
   double fac = 1.0;
   if (lambda < 0.5 * o->lambda0) {
-    fac = lambda > 0.0 ? pow(o->lambda0 / lambda, 0.2) : o->grow_max;
+    fac = lambda > 0.0 ? o->safety * pow(o->lambda0 / lambda, 0.2) : o->grow_max;
     if (fac > o->grow_max) fac = o->grow_max;
   }
   *dt_next = dt * fac;

@@ -47,6 +47,8 @@ typedef struct {
   double grow_max;    /* clamp on dt'/dt when growing */
   double shrink_min;  /* clamp on dt'/dt when shrinking */
   int max_rejects;    /* consecutive rejects before giving up */
+  double safety;      /* factor s on the adjusted step, s dt (L0/L)^0.2;
+                         1 is the law as printed */
 } ora_control_opts;
 
 /* --- spatial operator (section "Magnetic Field Relaxation", "Mimetic

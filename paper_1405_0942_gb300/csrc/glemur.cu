@@ -73,7 +73,8 @@ __device__ void set_coeffs(DevState* st) {
 }
 
 __global__ void k_reset_state(DevState* st, double dt0, double lambda0, double dt_min,
-                              double grow_max, double shrink_min, int max_rejects) {
+                              double grow_max, double shrink_min, int max_rejects,
+                              double safety) {
   st->dt = dt0;
   st->dt_last = 0.0;
   st->t = 0.0;
@@ -82,6 +83,7 @@ __global__ void k_reset_state(DevState* st, double dt0, double lambda0, double d
   st->dt_min = dt_min;
   st->grow_max = grow_max;
   st->shrink_min = shrink_min;
+  st->safety = safety;
   st->n_accept = 0;
   st->n_reject = 0;
   st->target = 0;
@@ -193,7 +195,7 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
     dtn = dt;
     st->replay = 0;
   } else if (lam > st->lambda0) {
-    double fac = pow(st->lambda0 / lam, 0.2);
+    double fac = st->safety * pow(st->lambda0 / lam, 0.2);
     if (fac < st->shrink_min) fac = st->shrink_min;
     accept = false;
     dtn = dt * fac;
@@ -207,7 +209,7 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
     accept = true;
     double fac = 1.0;
     if (lam < 0.5 * st->lambda0) {
-      fac = lam > 0.0 ? pow(st->lambda0 / lam, 0.2) : st->grow_max;
+      fac = lam > 0.0 ? st->safety * pow(st->lambda0 / lam, 0.2) : st->grow_max;
       if (fac > st->grow_max) fac = st->grow_max;
     }
     dtn = dt * fac;
@@ -509,7 +511,7 @@ int seed_stage_inputs(glemur_ctx* c) {
 
 int reset_state(glemur_ctx* c) {
   k_reset_state<<<1, 1, 0, c->s>>>(c->st, c->o.dt0, c->o.lambda0, c->o.dt_min, c->o.grow_max,
-                                   c->o.shrink_min, c->o.max_rejects);
+                                   c->o.shrink_min, c->o.max_rejects, c->o.safety);
   return cuda_rc(cudaGetLastError());
 }
 
@@ -586,6 +588,7 @@ void glemur_default_opts(glemur_opts* o) {
   o->shrink_min = 0.1;
   o->max_rejects = 64;
   o->diag_each_attempt = 1;
+  o->safety = 1.0;
 }
 
 size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision) {
@@ -605,7 +608,8 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   if ((o.precision != GLEMUR_FP64 && o.precision != GLEMUR_MIXED) ||
       (o.curl != GLEMUR_CURL_MIMETIC && o.curl != GLEMUR_CURL_DIRECT) ||
       !(o.lambda0 > 0) || !(o.dt0 > 0) || !(o.dt_min >= 0) || !(o.grow_max >= 1) ||
-      !(o.shrink_min > 0 && o.shrink_min <= 1) || o.max_rejects < 0)
+      !(o.shrink_min > 0 && o.shrink_min <= 1) || o.max_rejects < 0 ||
+      !(o.safety > 0 && o.safety <= 1))
     return GLEMUR_ERR_BADARG;
   for (int a = 0; a < 3; ++a)
     if (!(hi[a] > lo[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a]))

@@ -47,7 +47,7 @@ struct DevState {
   double dt_last;     // step size of the last accepted attempt
   double t;           // time of the accepted state
   double lambda;      // error estimate of the last attempt
-  double lambda0, dt_min, grow_max, shrink_min;
+  double lambda0, dt_min, grow_max, shrink_min, safety;
   long long n_accept, n_reject;
   long long target;   // attempts stop (no-op) once n_accept reaches this
   int consec;         // consecutive rejections

@@ -541,3 +541,16 @@ def test_folded_trial_stage_rejects_the_attempt():
     x, dt, log, st, rc = ora.relax(g, X, B0, 3, dt_big, opts=ora.ControlOpts(lambda0=1e-6))
     assert rc == ora.OK and st["accepted"] == 3 and st["rejected"] >= 1
     assert log[0] <= 0.1 * dt_big * (1 + 1e-12)
+
+
+def test_step_control_safety_factor():
+    """s dt (Lambda_0/Lambda)^0.2 on rejection and growth; s = 1 is the law
+    as printed, and the middle band (Lambda_0/2 <= Lambda <= Lambda_0) keeps
+    dt for any s."""
+    o = ora.ControlOpts(lambda0=1e-6, safety=0.9)
+    rc, dtn, acc = ora.step_control(o, 2e-6, 1e-3)
+    assert acc == 0 and abs(dtn - 0.9e-3 * 0.5 ** 0.2) < 1e-18
+    rc, dtn, acc = ora.step_control(o, 0.25e-6, 1e-3)
+    assert acc == 1 and abs(dtn - 0.9e-3 * 4 ** 0.2) < 1e-18
+    rc, dtn, acc = ora.step_control(o, 0.7e-6, 1e-3)
+    assert acc == 1 and dtn == 1e-3
