@@ -205,6 +205,14 @@ struct Acc<float> {
 
 // ------------------------------------------------------------ x_s planes
 
+// One shared-memory point of the mimetic kernel's tiles: (x, y, z, pad) of
+// the stage input, or (B_x, B_y, B_z, 1/det G); a single 16-byte (float) or
+// two 16-byte (double) shared loads fetch a stencil neighbour.
+template <typename C>
+struct alignas(4 * sizeof(C)) V4 {
+  C x, y, z, w;
+};
+
 // The shared-memory points of a W x H tile (+halo) that this thread loads:
 // LP slots, each the in-plane offset gj*nx + gi of the node, or -1.
 template <int W, int H, int HALO>
@@ -263,6 +271,24 @@ struct PlaneRaw {
       }
     }
   }
+
+  // The same, into an array of (x, y, z, pad) points.
+  __device__ __forceinline__ void commit_aos(const C* ca, const int* off, V4<C>* __restrict__ dst) const {
+#pragma unroll
+    for (int t = 0; t < LP; ++t) {
+      if (off[t] < 0) continue;
+      const int p = threadIdx.x + t * NT;
+      C s3[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C s = v[t][c][0];
+#pragma unroll
+        for (int j = 0; j < S; ++j) s = fma(ca[j], v[t][c][j + 1], s);
+        s3[c] = s;
+      }
+      dst[p] = V4<C>{s3[0], s3[1], s3[2], (C)0};
+    }
+  }
 };
 
 // ------------------------------------------------------------ mimetic
@@ -304,18 +330,34 @@ __device__ __forceinline__ int bslot(int q) { return (q + BRING) % BRING; }
 
 // B (and 1/det G) at every node of plane q in the tile + halo 1.  Index-space
 // differences: central inside, second-order one-sided on boundary faces.
+template <typename C>
+__device__ __forceinline__ void vsub(const V4<C>& a, const V4<C>& b, C o[3]) {
+  o[0] = a.x - b.x;
+  o[1] = a.y - b.y;
+  o[2] = a.z - b.z;
+}
+// one-sided second-order difference 4 p1 - 3 p0 - p2 (lower face; the upper
+// face is its negative with p1, p2 the inner neighbours)
+template <typename C>
+__device__ __forceinline__ void vside(const V4<C>& p0, const V4<C>& p1, const V4<C>& p2, C sgn,
+                                      C o[3]) {
+  o[0] = sgn * (((C)4 * p1.x - (C)3 * p0.x) - p2.x);
+  o[1] = sgn * (((C)4 * p1.y - (C)3 * p0.y) - p2.y);
+  o[2] = sgn * (((C)4 * p1.z - (C)3 * p0.z) - p2.z);
+}
+
 template <typename T, typename C>
 __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, int k1,
-                                          const BPts& bp, const C* __restrict__ xs,
-                                          C* __restrict__ bs, bool diag, bool state,
+                                          const BPts& bp, const V4<C>* __restrict__ xs,
+                                          V4<C>* __restrict__ bs, bool diag, bool state,
                                           Acc<C>& acc) {
   const int N = a.nx * a.ny * a.nz;
-  const C* xq = xs + xslot(q) * 3 * XP;
-  const C* xm = xs + xslot(q - 1) * 3 * XP;
-  const C* xp = xs + xslot(q + 1) * 3 * XP;
-  const C* xm2 = xs + xslot(q - 2) * 3 * XP;
-  const C* xp2 = xs + xslot(q + 2) * 3 * XP;
-  C* bq = bs + bslot(q) * 4 * BP;
+  const V4<C>* xq = xs + xslot(q) * XP;
+  const V4<C>* xm = xs + xslot(q - 1) * XP;
+  const V4<C>* xp = xs + xslot(q + 1) * XP;
+  const V4<C>* xm2 = xs + xslot(q - 2) * XP;
+  const V4<C>* xp2 = xs + xslot(q + 2) * XP;
+  V4<C>* bq = bs + bslot(q) * BP;
   const C h20 = h2of<T, C>(a, 0), h21 = h2of<T, C>(a, 1), h22 = h2of<T, C>(a, 2);
   const int sz = q == 0 ? 1 : (q == a.nz - 1 ? 2 : 0);
   const int nq = q * a.nx * a.ny;
@@ -328,19 +370,24 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
     const int code = bp.code[t];
     const int sx = code & 3, sy = (code >> 2) & 3;
     C g[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const C* s = xq + c * XP;
-      g[0][c] = sx == 0 ? s[x0 + 1] - s[x0 - 1]
-              : sx == 1 ? ((C)4 * s[x0 + 1] - (C)3 * s[x0]) - s[x0 + 2]
-                        : ((C)3 * s[x0] - (C)4 * s[x0 - 1]) + s[x0 - 2];
-      g[1][c] = sy == 0 ? s[x0 + XW] - s[x0 - XW]
-              : sy == 1 ? ((C)4 * s[x0 + XW] - (C)3 * s[x0]) - s[x0 + 2 * XW]
-                        : ((C)3 * s[x0] - (C)4 * s[x0 - XW]) + s[x0 - 2 * XW];
-      g[2][c] = sz == 0 ? xp[c * XP + x0] - xm[c * XP + x0]
-              : sz == 1 ? ((C)4 * xp[c * XP + x0] - (C)3 * s[x0]) - xp2[c * XP + x0]
-                        : ((C)3 * s[x0] - (C)4 * xm[c * XP + x0]) + xm2[c * XP + x0];
-    }
+    if (sx == 0)
+      vsub(xq[x0 + 1], xq[x0 - 1], g[0]);
+    else if (sx == 1)
+      vside(xq[x0], xq[x0 + 1], xq[x0 + 2], (C)1, g[0]);
+    else
+      vside(xq[x0], xq[x0 - 1], xq[x0 - 2], (C)-1, g[0]);
+    if (sy == 0)
+      vsub(xq[x0 + XW], xq[x0 - XW], g[1]);
+    else if (sy == 1)
+      vside(xq[x0], xq[x0 + XW], xq[x0 + 2 * XW], (C)1, g[1]);
+    else
+      vside(xq[x0], xq[x0 - XW], xq[x0 - 2 * XW], (C)-1, g[1]);
+    if (sz == 0)
+      vsub(xp[x0], xm[x0], g[2]);
+    else if (sz == 1)
+      vside(xq[x0], xp[x0], xp2[x0], (C)1, g[2]);
+    else
+      vside(xq[x0], xm[x0], xm2[x0], (C)-1, g[2]);
     g[0][0] += h20;
     g[1][1] += h21;
     g[2][2] += h22;
@@ -353,11 +400,8 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
             b2 = (C)__ldg(&a.B0s[2 * N + n]);
     C B[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      B[c] = (g[0][c] * b0 + g[1][c] * b1 + g[2][c] * b2) * r;
-      bq[c * BP + p] = B[c];
-    }
-    bq[3 * BP + p] = r;
+    for (int c = 0; c < 3; ++c) B[c] = (g[0][c] * b0 + g[1][c] * b1 + g[2][c] * b2) * r;
+    bq[p] = V4<C>{B[0], B[1], B[2], r};
     if (own_plane && (code & 16)) {
       // eq. "magnetic energy": zeta halves per boundary index coordinate
       const int nb = ((code >> 5) & 3) + (sz != 0);
@@ -414,40 +458,36 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, co
 // Mimetic current and velocity at the tile's nodes of plane m.
 template <typename T, typename C, bool FINAL>
 __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, int m, int i0,
-                                            int j0, const C* __restrict__ xs,
-                                            const C* __restrict__ bs, const T* d, T* dout,
+                                            int j0, const V4<C>* __restrict__ xs,
+                                            const V4<C>* __restrict__ bs, const T* d, T* dout,
                                             const DevState* st, bool diag, Acc<C>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gi = i0 + tx, gj = j0 + ty;
   if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
   const int x0 = (ty + 2) * XW + (tx + 2);
   const int b0i = (ty + 1) * BW + (tx + 1);
-  const C* xq = xs + xslot(m) * 3 * XP;
-  const C* xm = xs + xslot(m - 1) * 3 * XP;
-  const C* xp = xs + xslot(m + 1) * 3 * XP;
-  const C* bq = bs + bslot(m) * 4 * BP;
-  const C* bm = bs + bslot(m - 1) * 4 * BP;
-  const C* bp = bs + bslot(m + 1) * 4 * BP;
-  C g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const C* s = xq + c * XP;
-    g0[c] = s[x0 + 1] - s[x0 - 1];
-    g1[c] = s[x0 + XW] - s[x0 - XW];
-    g2[c] = xp[c * XP + x0] - xm[c * XP + x0];
-    const C* b = bq + c * BP;
-    P0[c] = b[b0i + 1] - b[b0i - 1];
-    P1[c] = b[b0i + BW] - b[b0i - BW];
-    P2[c] = bp[c * BP + b0i] - bm[c * BP + b0i];
-    B[c] = b[b0i];
-  }
+  const V4<C>* xq = xs + xslot(m) * XP;
+  const V4<C>* xm = xs + xslot(m - 1) * XP;
+  const V4<C>* xp = xs + xslot(m + 1) * XP;
+  const V4<C>* bq = bs + bslot(m) * BP;
+  const V4<C>* bm = bs + bslot(m - 1) * BP;
+  const V4<C>* bp = bs + bslot(m + 1) * BP;
+  C g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
+  vsub(xq[x0 + 1], xq[x0 - 1], g0);
+  vsub(xq[x0 + XW], xq[x0 - XW], g1);
+  vsub(xp[x0], xm[x0], g2);
+  vsub(bq[b0i + 1], bq[b0i - 1], P0);
+  vsub(bq[b0i + BW], bq[b0i - BW], P1);
+  vsub(bp[b0i], bm[b0i], P2);
+  const V4<C> bc = bq[b0i];
+  const C B[3] = {bc.x, bc.y, bc.z};
   g0[0] += h2of<T, C>(a, 0);
   g1[1] += h2of<T, C>(a, 1);
   g2[2] += h2of<T, C>(a, 2);
   const C c0 = dot3(P1, g2) - dot3(P2, g1);
   const C c1 = dot3(P2, g0) - dot3(P0, g2);
   const C c2 = dot3(P0, g1) - dot3(P1, g0);
-  const C r = bq[3 * BP + b0i];
+  const C r = bc.w;
   C J[3], u[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
@@ -481,10 +521,10 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
   constexpr bool FINAL = S == 5;
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
-  C* xs = reinterpret_cast<C*>(smem_raw);  // [XRING][3][XP]
-  C* bs = xs + XRING * 3 * XP;             // [BRING][B0,B1,B2,1/det][BP]
+  V4<C>* xs = reinterpret_cast<V4<C>*>(smem_raw);  // [XRING][XP] (x, y, z, -)
+  V4<C>* bs = xs + XRING * XP;                      // [BRING][BP] (B, 1/det G)
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
   const int cur = st->cur;
@@ -505,7 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
     if (q < 0 || q >= a.nz || q > k1 + 1) continue;
     Raw raw;
     raw.issue(a, d, pts.off, q);
-    raw.template commit<XP>(ca, pts.off, xs + xslot(q) * 3 * XP);
+    raw.commit_aos(ca, pts.off, xs + xslot(q) * XP);
   }
   __syncthreads();
   for (int q = k0 - 1; q <= k0 + 1; ++q)
@@ -521,7 +561,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
     if (qb < a.nz && qb <= k1)
       compute_B<T, C>(a, qb, k0, k1, bp, xs, bs, diag, S == 0, acc);
     mimetic_out<T, C, FINAL>(a, S, m, i0, j0, xs, bs, d, dout, st, diag, acc);
-    if (load) raw.template commit<XP>(ca, pts.off, xs + xslot(qn) * 3 * XP);
+    if (load) raw.commit_aos(ca, pts.off, xs + xslot(qn) * XP);
     __syncthreads();
   }
   write_partials<T, C>(a, FINAL, diag, acc, red);
@@ -675,7 +715,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
 // ------------------------------------------------------------ launchers
 
 inline size_t stage_smem_bytes(int curl, size_t csize) {
-  return curl == 0 ? (size_t)(XRING * 3 * XP + BRING * 4 * BP) * csize
+  return curl == 0 ? (size_t)(XRING * XP + BRING * BP) * 4 * csize
                    : (size_t)(3 * 3 * DP) * csize;
 }
 
@@ -685,7 +725,7 @@ cudaError_t launch_stage_t(const StageArgs<T>& a, int stage, dim3 grid, cudaStre
   const size_t smem = stage_smem_bytes(CURL, sizeof(C));
 #define GLEMUR_STAGE_CASE(SS)                                              \
   case SS:                                                                 \
-    if (CURL == 0)                                                         \
+    if constexpr (CURL == 0)                                               \
       k_stage_mimetic<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);           \
     else                                                                   \
       k_stage_direct<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);            \
@@ -709,11 +749,14 @@ cudaError_t prepare_stage_t() {
   const int sm = (int)stage_smem_bytes(CURL, sizeof(C));
   cudaError_t e = cudaSuccess;
 #define GLEMUR_PREP(SS)                                                                  \
-  if (e == cudaSuccess)                                                                  \
-    e = CURL == 0 ? cudaFuncSetAttribute(k_stage_mimetic<T, C, SS, MINB>,                \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm) \
-                  : cudaFuncSetAttribute(k_stage_direct<T, C, SS, MINB>,                 \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) {                                                                \
+    if constexpr (CURL == 0)                                                             \
+      e = cudaFuncSetAttribute(k_stage_mimetic<T, C, SS, MINB>,                          \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+    else                                                                                 \
+      e = cudaFuncSetAttribute(k_stage_direct<T, C, SS, MINB>,                           \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, sm);         \
+  }
   GLEMUR_PREP(0)
   GLEMUR_PREP(1)
   GLEMUR_PREP(2)
@@ -728,7 +771,7 @@ template <typename T, typename C, int CURL, int MINB>
 int stage_ctas_per_sm_t() {
   int n = 0;
   const size_t s = stage_smem_bytes(CURL, sizeof(C));
-  if (CURL == 0)
+  if constexpr (CURL == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_mimetic<T, C, 3, MINB>, NT, s);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_direct<T, C, 3, MINB>, NT, s);
