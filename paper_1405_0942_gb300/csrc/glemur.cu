@@ -306,7 +306,7 @@ struct glemur_ctx {
   double* part;     // NPART * max_blocks
   DevState* st;
   int split;                             // FP64 mimetic stages in two passes
-  double* ys[2];                         // split path: stage inputs
+  void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
   double* rb;                            // split path: 1/det G
   int max_blocks, nblocks, kz;          // mimetic-current launches
@@ -340,10 +340,11 @@ Layout layout(int nx, int ny, int nz, int precision) {
   L.part = align256((size_t)NPART * L.max_blocks * sizeof(double));
   L.state = align256(sizeof(DevState));
   L.ptrs = 256;
-  // FP64: two stage inputs, B and 1/det G for the two-pass stages
-  L.split = precision == GLEMUR_FP64 ? 3 * align256((size_t)(3 * N) * 8) +
-                                           align256((size_t)N * 8)
-                                     : 0;
+  // two stage inputs (mimetic stages); FP64 also B and 1/det G for the
+  // two-pass stages
+  L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
+                                                          align256((size_t)N * 8)
+                                                    : 0);
   L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.split;
   return L;
 }
@@ -408,6 +409,8 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.B0s = (const T*)c->B0s;
   for (int j = 0; j < 5; ++j) a.k[j] = (T*)c->k[j];
   a.k6 = nullptr;
+  a.ys[0] = (T*)c->ys[0];
+  a.ys[1] = (T*)c->ys[1];
   a.stage = stage;
   a.diag = diag;
   a.force = force;
@@ -432,8 +435,8 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.B0s = (const double*)c->B0s;
   for (int j = 0; j < 5; ++j) a.k[j] = (double*)c->k[j];
   a.k[5] = (double*)k6;
-  a.ys[0] = c->ys[0];
-  a.ys[1] = c->ys[1];
+  a.ys[0] = (double*)c->ys[0];
+  a.ys[1] = (double*)c->ys[1];
   a.Bb = c->Bb;
   a.rb = c->rb;
   a.diag = diag;
@@ -499,11 +502,11 @@ void fill_stats(const DevState& hs, int curl, glemur_stats* out) {
   out->dt_last = hs.dt_last;
 }
 
-// The two-pass FP64 stages write stage inputs at interior nodes only; the
+// The mimetic stages write stage inputs at interior nodes only; the
 // boundary entries must hold the (fixed) boundary positions.
 int seed_stage_inputs(glemur_ctx* c) {
   if (!c->ys[0]) return GLEMUR_OK;
-  const size_t n = sizeof(double) * 3 * c->N;
+  const size_t n = c->esize * 3 * c->N;
   cudaError_t e = cudaMemcpyAsync(c->ys[0], c->dbuf[0], n, cudaMemcpyDeviceToDevice, c->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->ys[1], c->dbuf[0], n, cudaMemcpyDeviceToDevice, c->s);
   return cuda_rc(e);
@@ -646,11 +649,10 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->max_blocks = L.max_blocks;
   c->split = 0;
   c->ys[0] = c->ys[1] = c->Bb = c->rb = nullptr;
-  if (L.split) {
-    const size_t f8 = align256((size_t)(3 * c->N) * 8);
-    c->ys[0] = (double*)p; p += f8;
-    c->ys[1] = (double*)p; p += f8;
-    c->Bb = (double*)p; p += f8;
+  c->ys[0] = p; p += L.field;
+  c->ys[1] = p; p += L.field;
+  if (o.precision == GLEMUR_FP64) {
+    c->Bb = (double*)p; p += align256((size_t)(3 * c->N) * 8);
     c->rb = (double*)p;
     const char* fused = getenv("GLEMUR_F64_FUSED");
     c->split = !(fused && atoi(fused) > 0);

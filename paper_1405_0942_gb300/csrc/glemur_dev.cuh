@@ -80,6 +80,8 @@ struct StageArgs {
   const T* B0s;        // pre-scaled B0 (3N)
   T* k[5];             // stage derivatives k1..k5 (3N each)
   T* k6;               // if set, the last stage also stores k6 here
+  T* ys[2];            // stage inputs: y_s in ys[s & 1] (s >= 1), 3N each;
+                       // boundary entries hold the fixed boundary positions
   int stage;           // 0..5 (stage s+1 of Cash-Karp)
   int diag;            // reduce E_M / xi partials in this launch
   int force;           // run even if the step target is reached

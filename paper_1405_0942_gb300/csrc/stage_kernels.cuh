@@ -22,12 +22,16 @@
 // with c_r the right-hand sides: the same J as the paper's loop form, with
 // no 3x3 solve and det G the one the pull-back already needs.
 //
-// Pipeline (mimetic kernel).  Shared memory holds a ring of 6 planes of x_s
-// and a ring of 4 planes of B.  Iteration m computes B at plane m+2, the
-// current at plane m and the stage input of plane m+4: the three touch
-// disjoint ring slots, so one barrier per plane suffices, and the global
-// loads of plane m+4 are issued before, and committed after, the arithmetic
-// of the other two.
+// Pipeline (mimetic kernel).  Stage s reads its input y_s (written pointwise
+// by stage s-1; y_0 = x) with halos, and writes k_s and, at its own nodes,
+// the next input y_{s+1} = d + sum_{j<=s} dt a_{s+1,j} k_j -- so the halo
+// tiles carry one field, and the combine runs once per node.  Shared memory
+// holds a ring of 6 planes of y_s and a ring of 4 planes of B.  Iteration m
+// computes B at plane m+2, the current at plane m and loads plane m+4 of
+// y_s: the three touch disjoint ring slots, so one barrier per plane
+// suffices.  The global loads of y (plane m+4), of B0 (plane m+3) and of the
+// centre values for y_{s+1} (plane m) are issued ahead of the arithmetic
+// that hides their latency.
 //
 // Direct current (the classic method).  dB/dX follows from B = G B0s / det G
 // by the product rule with second differences of x, differences of B0s and
@@ -291,6 +295,49 @@ struct PlaneRaw {
   }
 };
 
+// One plane of a single displacement-like field (the stage input y) at the
+// thread's tile points, held in registers between issue and commit.
+template <typename T, typename C, int LP>
+struct YPlane {
+  C v[LP][3];
+  __device__ __forceinline__ void issue(const T* __restrict__ y, int N, int nxy, const int* off,
+                                        int q) {
+    const int base = q * nxy;
+#pragma unroll
+    for (int t = 0; t < LP; ++t) {
+      if (off[t] < 0) continue;
+      const int n = base + off[t];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[t][c] = (C)__ldg(&y[c * N + n]);
+    }
+  }
+  __device__ __forceinline__ void commit(const int* off, V4<C>* __restrict__ dst) const {
+#pragma unroll
+    for (int t = 0; t < LP; ++t)
+      if (off[t] >= 0) dst[threadIdx.x + t * NT] = V4<C>{v[t][0], v[t][1], v[t][2], (C)0};
+  }
+};
+
+// Centre values a stage output needs at its node: d and the k_j of the next
+// stage input (stage S < 5: k_0..k_{S-1}), or of the update and error
+// (S = 5: k1, k3, k4, k5).
+template <typename T, typename C, int S>
+struct Centre {
+  static constexpr int NK = S == 5 ? 4 : S;
+  C d[3];
+  C k[NK > 0 ? NK : 1][3];
+  __device__ __forceinline__ static int kidx(int j) { return S == 5 ? (j == 0 ? 0 : j + 1) : j; }
+  __device__ __forceinline__ void issue(const StageArgs<T>& a, const T* __restrict__ dsrc, int N,
+                                        int n) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = (C)__ldg(&dsrc[c * N + n]);
+#pragma unroll
+      for (int j = 0; j < NK; ++j) k[j][c] = (C)__ldg(&a.k[kidx(j)][c * N + n]);
+    }
+  }
+};
+
 // ------------------------------------------------------------ mimetic
 
 // The B-tile points this thread computes (tile + halo 1, at most BPT), with
@@ -346,12 +393,32 @@ __device__ __forceinline__ void vside(const V4<C>& p0, const V4<C>& p1, const V4
   o[2] = sgn * (((C)4 * p1.z - (C)3 * p0.z) - p2.z);
 }
 
+template <typename C>
+struct B0Pts {
+  C v[BPts::BPT][3];
+};
+
+// B0s at the thread's B points of plane q.
+template <typename T, typename C>
+__device__ __forceinline__ void load_B0(const StageArgs<T>& a, int q, const BPts& bp,
+                                        B0Pts<C>& out) {
+  const int N = a.nx * a.ny * a.nz;
+  const int nq = q * a.nx * a.ny;
+#pragma unroll
+  for (int t = 0; t < BPts::BPT; ++t) {
+    if (bp.x0[t] < 0) continue;
+    const int n = nq + bp.nxy[t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out.v[t][c] = (C)__ldg(&a.B0s[c * N + n]);
+  }
+}
+
 template <typename T, typename C>
 __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, int k1,
-                                          const BPts& bp, const V4<C>* __restrict__ xs,
+                                          const BPts& bp, const B0Pts<C>& b0v,
+                                          const V4<C>* __restrict__ xs,
                                           V4<C>* __restrict__ bs, bool diag, bool state,
                                           Acc<C>& acc) {
-  const int N = a.nx * a.ny * a.nz;
   const V4<C>* xq = xs + xslot(q) * XP;
   const V4<C>* xm = xs + xslot(q - 1) * XP;
   const V4<C>* xp = xs + xslot(q + 1) * XP;
@@ -360,7 +427,6 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
   V4<C>* bq = bs + bslot(q) * BP;
   const C h20 = h2of<T, C>(a, 0), h21 = h2of<T, C>(a, 1), h22 = h2of<T, C>(a, 2);
   const int sz = q == 0 ? 1 : (q == a.nz - 1 ? 2 : 0);
-  const int nq = q * a.nx * a.ny;
   const bool own_plane = diag && q >= k0 && q < k1;
 #pragma unroll
   for (int t = 0; t < BPts::BPT; ++t) {
@@ -395,9 +461,7 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
     if (det <= (C)0)  // NaN: reported by the error norm
       atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
     const C r = recip(det);
-    const int n = nq + bp.nxy[t];
-    const C b0 = (C)__ldg(&a.B0s[n]), b1 = (C)__ldg(&a.B0s[N + n]),
-            b2 = (C)__ldg(&a.B0s[2 * N + n]);
+    const C b0 = b0v.v[t][0], b1 = b0v.v[t][1], b2 = b0v.v[t][2];
     C B[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) B[c] = (g[0][c] * b0 + g[1][c] * b1 + g[2][c] * b2) * r;
@@ -455,15 +519,66 @@ __device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, co
   }
 }
 
-// Mimetic current and velocity at the tile's nodes of plane m.
-template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, int m, int i0,
-                                            int j0, const V4<C>* __restrict__ xs,
-                                            const V4<C>* __restrict__ bs, const T* d, T* dout,
+// Stage-S output at node n from its centre values: k_S and the next stage
+// input, or (S = 5) the update, the error and (optionally) k6.
+template <typename T, typename C, int S>
+__device__ __forceinline__ void emit_centre(const StageArgs<T>& a, int n, const C u[3],
+                                            const C J[3], const C B[3],
+                                            const Centre<T, C, S>& ce, T* __restrict__ dout,
+                                            const C* an, const DevState* st, bool diag,
+                                            Acc<C>& acc) {
+  const int N = a.nx * a.ny * a.nz;
+  if (diag) {
+    const C u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
+    // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
+    if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
+    const C jb = j2 * b2;
+    if (jb > (C)0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+  }
+  if constexpr (S < 5) {
+    T* ko = a.k[S];
+    T* ynext = a.ys[(S + 1) & 1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ko[c * N + n] = (T)u[c];
+      C v = ce.d[c];
+#pragma unroll
+      for (int j = 0; j < S; ++j) v = fma(an[j], ce.k[j][c], v);
+      ynext[c * N + n] = (T)fma(an[S], u[c], v);
+    }
+  } else {
+    // fifth-order update (b_2 = b_5 = 0) and embedded error (b_2 - b*_2 = 0)
+    const C b0 = coef_b<C>(st, 0), b2 = coef_b<C>(st, 2), b3 = coef_b<C>(st, 3),
+            b5 = coef_b<C>(st, 5);
+    const C e0 = coef_e<C>(st, 0), e2 = coef_e<C>(st, 2), e3 = coef_e<C>(st, 3),
+            e4 = coef_e<C>(st, 4), e5 = coef_e<C>(st, 5);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C k1 = ce.k[0][c], k3 = ce.k[1][c], k4 = ce.k[2][c], k5 = ce.k[3][c];
+      C up = b0 * k1;
+      up = fma(b2, k3, up);
+      up = fma(b3, k4, up);
+      up = fma(b5, u[c], up);
+      C er = e0 * k1;
+      er = fma(e2, k3, er);
+      er = fma(e3, k4, er);
+      er = fma(e4, k5, er);
+      er = fma(e5, u[c], er);
+      dout[c * N + n] = (T)(ce.d[c] + up);
+      acc.max_lam(fabs(er));
+      if (a.k6) a.k6[c * N + n] = (T)u[c];
+    }
+  }
+}
+
+// Mimetic current and velocity at the thread's node (gi, gj) of plane m.
+template <typename T, typename C, int S>
+__device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int m, int n,
+                                            const V4<C>* __restrict__ xs,
+                                            const V4<C>* __restrict__ bs,
+                                            const Centre<T, C, S>& ce, T* dout, const C* an,
                                             const DevState* st, bool diag, Acc<C>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gi = i0 + tx, gj = j0 + ty;
-  if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
   const int x0 = (ty + 2) * XW + (tx + 2);
   const int b0i = (ty + 1) * BW + (tx + 1);
   const V4<C>* xq = xs + xslot(m) * XP;
@@ -494,7 +609,7 @@ __device__ __forceinline__ void mimetic_out(const StageArgs<T>& a, int stage, in
   u[0] = J[1] * B[2] - J[2] * B[1];
   u[1] = J[2] * B[0] - J[0] * B[2];
   u[2] = J[0] * B[1] - J[1] * B[0];
-  emit<T, C, FINAL>(a, stage, (m * a.ny + gj) * a.nx + gi, u, J, B, d, dout, st, diag, acc);
+  emit_centre<T, C, S>(a, n, u, J, B, ce, dout, an, st, diag, acc);
 }
 
 template <typename T, typename C>
@@ -523,45 +638,61 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
-  V4<C>* xs = reinterpret_cast<V4<C>*>(smem_raw);  // [XRING][XP] (x, y, z, -)
+  V4<C>* xs = reinterpret_cast<V4<C>*>(smem_raw);  // [XRING][XP] (y_s, -)
   V4<C>* bs = xs + XRING * XP;                      // [BRING][BP] (B, 1/det G)
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
+  const int N = a.nx * a.ny * a.nz, nxy = a.nx * a.ny;
   const int cur = st->cur;
   const T* d = a.d[cur];
   T* dout = const_cast<T*>(a.d[cur ^ 1]);
-  C ca[S > 0 ? S : 1];
+  const T* y = S == 0 ? d : a.ys[S & 1];
+  C an[S < 5 ? S + 1 : 1];  // dt a_{S+1, j}: the next stage input
 #pragma unroll
-  for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
+  for (int j = 0; j < (S < 5 ? S + 1 : 0); ++j) an[j] = coef_a<C>(st, S + 1, j);
   const bool diag = a.diag != 0;
   Acc<C> acc;
   LoadPts<XW, XH, 2> pts;
   pts.init(i0, j0, a.nx, a.ny);
   BPts bp;
   bp.init(i0, j0, a.nx, a.ny);
-  using Raw = PlaneRaw<T, C, S, LoadPts<XW, XH, 2>::LP>;
-  // prologue: stage input planes k0-2 .. k0+3, then B at k0-1 .. k0+1
+  using Y = YPlane<T, C, LoadPts<XW, XH, 2>::LP>;
+  // the thread's own output column
+  const int gi = i0 + threadIdx.x % TX, gj = j0 + threadIdx.x / TX;
+  const bool out_xy = gi >= 1 && gi <= a.nx - 2 && gj >= 1 && gj <= a.ny - 2;
+  const int nxy_out = gj * a.nx + gi;
+  // prologue: input planes k0-2 .. k0+3, then B at k0-1 .. k0+1
   for (int q = k0 - 2; q <= k0 + 3; ++q) {
     if (q < 0 || q >= a.nz || q > k1 + 1) continue;
-    Raw raw;
-    raw.issue(a, d, pts.off, q);
-    raw.commit_aos(ca, pts.off, xs + xslot(q) * XP);
+    Y yp;
+    yp.issue(y, N, nxy, pts.off, q);
+    yp.commit(pts.off, xs + xslot(q) * XP);
   }
   __syncthreads();
   for (int q = k0 - 1; q <= k0 + 1; ++q)
-    if (q >= 0 && q < a.nz && q <= k1)
-      compute_B<T, C>(a, q, k0, k1, bp, xs, bs, diag, S == 0, acc);
+    if (q >= 0 && q < a.nz && q <= k1) {
+      B0Pts<C> b0v;
+      load_B0(a, q, bp, b0v);
+      compute_B<T, C>(a, q, k0, k1, bp, b0v, xs, bs, diag, S == 0, acc);
+    }
+  B0Pts<C> b0cur;
+  if (k0 + 2 < a.nz && k0 + 2 <= k1) load_B0(a, k0 + 2, bp, b0cur);
   __syncthreads();
   for (int m = k0; m < k1; ++m) {
-    const int qn = m + 4;  // stage input plane loaded in this iteration
+    const int qn = m + 4;  // input plane loaded in this iteration
     const bool load = qn < a.nz && qn <= k1 + 1;
-    Raw raw;
-    if (load) raw.issue(a, d, pts.off, qn);
+    const bool out = out_xy && m >= 1 && m <= a.nz - 2;
+    const int n = m * nxy + nxy_out;
+    Y yp;
+    if (load) yp.issue(y, N, nxy, pts.off, qn);
+    Centre<T, C, S> ce;
+    if (out) ce.issue(a, d, N, n);
     const int qb = m + 2;  // B plane computed in this iteration
     if (qb < a.nz && qb <= k1)
-      compute_B<T, C>(a, qb, k0, k1, bp, xs, bs, diag, S == 0, acc);
-    mimetic_out<T, C, FINAL>(a, S, m, i0, j0, xs, bs, d, dout, st, diag, acc);
-    if (load) raw.commit_aos(ca, pts.off, xs + xslot(qn) * XP);
+      compute_B<T, C>(a, qb, k0, k1, bp, b0cur, xs, bs, diag, S == 0, acc);
+    if (qb + 1 < a.nz && qb + 1 <= k1) load_B0(a, qb + 1, bp, b0cur);
+    if (out) mimetic_out<T, C, S>(a, m, n, xs, bs, ce, dout, an, st, diag, acc);
+    if (load) yp.commit(pts.off, xs + xslot(qn) * XP);
     __syncthreads();
   }
   write_partials<T, C>(a, FINAL, diag, acc, red);

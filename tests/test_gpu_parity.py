@@ -104,6 +104,30 @@ def test_one_step_fp64(G, curl):
     assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref
 
 
+@pytest.mark.parametrize("curl", [0, 1], ids=["mimetic", "direct"])
+@pytest.mark.parametrize("dims", [(24, 20, 28), (37, 19, 23)], ids=lambda d: "x".join(map(str, d)))
+def test_one_step_mixed(G, dims, curl):
+    """One Cash-Karp step of fixed size in mixed precision: all six stages
+    (each stage's input formed from the previous stages' FP32 k_j), the
+    update and the error norm.  The step's displacement carries the
+    velocity's 2e-4 relative error; the stored position adds FP32 rounding of
+    the displacement from the label grid."""
+    g, x0, B0 = braid_case(*dims)
+    X = gi.nodes(g)
+    dt = 2e-3
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, curl)
+    assert rc == ora.OK
+    r = relaxation(G, g, x0, B0, precision=1, curl=curl)
+    st = r.step_fixed(dt)
+    x = r.get_x().cpu().numpy()
+    assert st["accepted"] == 1
+    step = np.abs(x_ref - x0).max()
+    err = np.abs(x - x_ref).max()
+    assert err <= 3e-4 * step + 2e-7 * np.abs(x_ref - X).max(), (err, step)
+    # the error norm is a cancelling combination of the k_j: 5 % relative
+    assert abs(st["lam"] - lam_ref) <= 5e-2 * lam_ref, (st["lam"], lam_ref)
+
+
 def test_hundred_steps_replayed_schedule_fp64(G):
     """100 error-controlled steps of the oracle; the GPU replays the accepted
     step sizes: x within 1e-10 relative."""
