@@ -43,9 +43,14 @@ ALGO_BYTES = {"fp64": 132.0, "mixed": 66.0}
 ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0}
 FP64_PEAK_FLOPS = 1.25e12      # nominal dense FP64 rate of GB300 (152 SMs)
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes per stage launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum); None until a capture of the current kernels exists
-NCU_TRAFFIC = {}
+# DRAM bytes per stage from ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# of one attempt's six stages, averaged; FP64: both passes of a stage), keyed
+# by (n, precision, curl); absent workloads report null
+NCU_TRAFFIC = {
+    (64, "fp64", "mimetic"): 45.86e6,
+    (64, "mixed", "mimetic"): 15.74e6,
+    (128, "mixed", "mimetic"): 154.07e6,
+}
 
 
 def load_peaks():
