@@ -321,7 +321,9 @@ def our_arm(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded braid field and pre-distorted grid)",
         "config": config_dict(args, w), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-        "clocks": clocks, "gpu_launches": r.kernels_per_attempt() * args.steps,
+        "clocks": clocks,
+        # per timed attempt: the target reset plus the attempt's kernels
+        "gpu_launches": (r.kernels_per_attempt() + 1) * args.steps,
         "kernel_ms": {"stages": per_kernel[:6], "control": per_kernel[6]},
         "attempts": {"accepted": st["accepted"], "rejected": st["rejected"]},
         "compare": extra,

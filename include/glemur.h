@@ -199,12 +199,13 @@ int glemur_get_stats(glemur_ctx* ctx, glemur_stats* stats);
 /* Number of CUDA kernels one attempt launches (for launch accounting). */
 int glemur_kernels_per_attempt(const glemur_ctx* ctx);
 
-/* Enqueue one attempt exactly as glemur_attempts(ctx, 1) does, with a CUDA
- * event recorded on the context's stream before each of its kernels and
- * after the last; synchronise and write the kernels' durations in
- * milliseconds to ms[0 .. n-1] in launch order (Cash-Karp stages 1..6, then
- * the step control), n = glemur_kernels_per_attempt(ctx) <= cap.  Returns n,
- * or a negative error (BADARG if cap < n). */
+/* Enqueue one attempt exactly as glemur_attempts(ctx, 1) does (one
+ * target-reset kernel, then glemur_kernels_per_attempt(ctx) kernels), with a
+ * CUDA event recorded on the context's stream before each Cash-Karp stage,
+ * before the step control and after it; synchronise and write the 7
+ * intervals in milliseconds to ms[0..6]: stages 1..6 (each interval covers
+ * all kernels of its stage: two for the FP64 two-pass stages), then the
+ * control.  Returns 7, or a negative error (BADARG if cap < 7). */
 int glemur_profile_attempt(glemur_ctx* ctx, float* ms, int cap);
 
 /* ---- adjoint (reverse mode) of the relaxation, mimetic current ---------

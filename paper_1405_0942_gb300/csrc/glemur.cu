@@ -41,6 +41,7 @@ struct SplitArgs {
   int nblocks;
 };
 cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s);
+int split_ctas_per_sm();
 
 // Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
 // of section "Time Stepping".
@@ -675,9 +676,9 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
   c->nblocks = gx * gy * (int)c->grid.z;
   if (c->split) {
-    // grid-stride passes: up to 4 CTAs of 256 threads per SM
+    // one wave of CTAs of 256 threads, each over an equal range of node warps
     const long long need = (c->N + 255) / 256;
-    const long long cap = 4LL * c->nsm;
+    const long long cap = (long long)split_ctas_per_sm() * c->nsm;
     c->nblocks = (int)(need < cap ? need : cap);
   }
   c->kz_direct = choose_kz(nz, gx * gy, c->nsm, pd, !mixed);

@@ -16,9 +16,11 @@
 //            k_s and, pointwise, the next stage input
 //            y_{s+1} = d + sum_{j<=s} dt a_{s+1,j} k_j; the last stage
 //            writes the fifth-order update and the embedded error instead.
-// Both are grid-stride kernels over a fixed number of CTAs, so every SM is
-// busy; the per-CTA partials (Lambda, E_M, xi) keep the fused kernel's
-// layout.
+// Both run one wave of CTAs (as many as fit on the SMs), each over a
+// contiguous range of whole warps of nodes: the FP64 pipe is per SM, so
+// every SM gets the same number of node-warps (to within one per CTA) and
+// no SM idles while another finishes a second round.  The per-CTA partials
+// (Lambda, E_M, xi) keep the fused kernel's layout.
 #include "stage_kernels.cuh"
 
 namespace glemur {
@@ -38,6 +40,15 @@ struct SplitArgs {
   double* part;
   int nblocks;
 };
+
+// This CTA's node range: warps [W b / G, W (b+1) / G) of the W = N/32 node
+// warps (rounded up), as node indices [begin, end).
+__device__ __forceinline__ void cta_range(int N, int& begin, int& end) {
+  const long long W = (N + 31) / 32;
+  const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+  begin = (int)(w0 * 32);
+  end = (int)(w1 * 32 < N ? w1 * 32 : N);
+}
 
 __device__ __forceinline__ void split_nodes(const SplitArgs& a, int n, int& i, int& j, int& k) {
   i = n % a.nx;
@@ -76,7 +87,9 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   const int N = a.nx * a.ny * a.nz;
   const double* y = S == 0 ? a.d[st->cur] : a.ys[S & 1];
   double eacc = 0.0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+  int nb, ne;
+  cta_range(N, nb, ne);
+  for (int n = nb + threadIdx.x; n < ne; n += blockDim.x) {
     int i, j, k;
     split_nodes(a, n, i, j, k);
     double g0[3], g1[3], g2[3];
@@ -128,7 +141,9 @@ __global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
   for (int j = 0; j < 5; ++j) an[j] = (!FINAL && j <= S) ? st->dta[S + 1][j] : 0.0;
   Acc<double> acc;
   const int sy = a.nx, sz = a.nx * a.ny;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+  int nb, ne;
+  cta_range(N, nb, ne);
+  for (int n = nb + threadIdx.x; n < ne; n += blockDim.x) {
     int i, j, k;
     split_nodes(a, n, i, j, k);
     if (i < 1 || i > a.nx - 2 || j < 1 || j > a.ny - 2 || k < 1 || k > a.nz - 2) continue;
@@ -209,6 +224,15 @@ __global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
     v = block_reduce<true>(acc.xis2, red);
     if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
   }
+}
+
+// CTAs of 256 threads per SM that both passes can hold at once.
+int split_ctas_per_sm() {
+  int b = 0, c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_split_B<0>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_split_C<5>, 256, 0);
+  const int m = b < c ? b : c;
+  return m > 0 ? m : 1;
 }
 
 // Launch both passes of stage s on `nblocks` CTAs of 256 threads.
