@@ -68,8 +68,10 @@ enum glemur_status {
   GLEMUR_ERR_DT_UNDERFLOW = -5, /* step shrank below dt_min or too many
                                    consecutive rejections */
   GLEMUR_ERR_WORKSPACE = -6,    /* workspace missing, misaligned or small */
-  GLEMUR_ERR_TOO_LARGE = -7     /* grid larger than a fixed-scratch entry
+  GLEMUR_ERR_TOO_LARGE = -7,    /* grid larger than a fixed-scratch entry
                                    point supports */
+  GLEMUR_ERR_TIMEOUT = -8       /* a bounded device-side wait for a tile
+                                   load gave up; the state is not advanced */
 };
 
 typedef struct glemur_ctx glemur_ctx;

@@ -9,8 +9,11 @@
 #include <cstring>
 #include <new>
 
+#include <cudaTypedefs.h>
+
 #include "glemur.h"
 #include "glemur_dev.cuh"
+#include "tma.cuh"
 
 namespace glemur {
 cudaError_t launch_f64_mimetic(const StageArgs<double>& a, int stage, dim3 grid, cudaStream_t s);
@@ -25,6 +28,10 @@ int ctas_per_sm_f64_mimetic();
 int ctas_per_sm_f64_direct();
 int ctas_per_sm_f32_mimetic();
 int ctas_per_sm_f32_direct();
+cudaError_t launch_f32_mimetic_tma(const StageArgs<float>& a, const TmaMaps& maps, int stage,
+                                   dim3 grid, cudaStream_t s);
+cudaError_t prepare_f32_mimetic_tma();
+int ctas_per_sm_f32_mimetic_tma();
 
 struct SplitArgs {
   int nx, ny, nz;
@@ -146,6 +153,7 @@ __device__ void finalize_diag(DevState* st, const double* part, int nb, double* 
 __global__ void k_diag_finalize(DevState* st, const double* part, int nb) {
   __shared__ double sh[96];
   finalize_diag(st, part, nb, sh);
+  if (threadIdx.x == 0 && (st->flags & FLAG_TIMEOUT)) st->status = ST_TIMEOUT;
 }
 
 // Eq. "time stepping" and the acceptance rule around it, after each attempt.
@@ -167,6 +175,11 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
   const double lam = sh[95];
   const double dt = st->dt;
   st->lambda = lam;
+  if (st->flags & FLAG_TIMEOUT) {
+    st->status = ST_TIMEOUT;
+    st->n_reject++;
+    return;
+  }
   if (st->flags & FLAG_COLLAPSED) {
     st->status = ST_COLLAPSED;
     st->n_reject++;
@@ -307,6 +320,8 @@ struct glemur_ctx {
   double* part;     // NPART * max_blocks
   DevState* st;
   int split;                             // FP64 mimetic stages in two passes
+  int tma;                               // mixed mimetic stages with TMA tiles
+  TmaMaps maps;                          // their tensor maps
   void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
   double* rb;                            // split path: 1/det G
@@ -460,6 +475,7 @@ cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int
       a.nblocks = c->nblocks_direct;
       return launch_f32_direct(a, stage, g, c->s);
     }
+    if (c->tma) return launch_f32_mimetic_tma(a, c->maps, stage, g, c->s);
     return launch_f32_mimetic(a, stage, g, c->s);
   }
   StageArgs<double> a = make_args<double>(c, stage, diag, force);
@@ -540,6 +556,53 @@ int stage_out(glemur_ctx* c, double* dst, int mem) {
                                   cudaMemcpyDeviceToHost, c->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
   return cuda_rc(e);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 4-D map (x, y, z, component) of an FP32 SoA field with boxes of
+// YW x box_h x 1 x 3; out-of-range elements read as zero.
+bool encode_field_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, void* base,
+                      int nx, int ny, int nz, int box_h) {
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4,
+                                 (cuuint64_t)nx * ny * nz * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)YW, (cuuint32_t)box_h, 1, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA tiles for the mixed mimetic stages: rows 16-byte aligned (nx a
+// multiple of 4) and a grid at least one box wide and high.
+bool setup_tma(glemur_ctx* c) {
+  if (c->o.precision != GLEMUR_MIXED || c->nx % 4 || c->nx < YW || c->ny < YH) return false;
+  const char* env = getenv("GLEMUR_TMA");
+  if (env && atoi(env) == 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  bool ok = true;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = encode_field_map(enc, &c->maps.d[i], c->dbuf[i], c->nx, c->ny, c->nz, YH) &&
+         encode_field_map(enc, &c->maps.ys[i], c->ys[i], c->nx, c->ny, c->nz, YH);
+  return ok && encode_field_map(enc, &c->maps.b0, c->B0s, c->nx, c->ny, c->nz, ZH);
 }
 
 }  // namespace
@@ -664,13 +727,19 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
   const bool mixed = o.precision == GLEMUR_MIXED;
   if (e == cudaSuccess) e = mixed ? prepare_f32_mimetic() : prepare_f64_mimetic();
+  c->tma = 0;
+  if (e == cudaSuccess && setup_tma(c)) {
+    e = prepare_f32_mimetic_tma();
+    c->tma = 1;
+  }
   if (e == cudaSuccess) e = mixed ? prepare_f32_direct() : prepare_f64_direct();
   if (e != cudaSuccess) {
     delete c;
     return GLEMUR_ERR_CUDA;
   }
   const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
-  const int pm = mixed ? ctas_per_sm_f32_mimetic() : ctas_per_sm_f64_mimetic();
+  const int pm = mixed ? (c->tma ? ctas_per_sm_f32_mimetic_tma() : ctas_per_sm_f32_mimetic())
+                       : ctas_per_sm_f64_mimetic();
   const int pd = mixed ? ctas_per_sm_f32_direct() : ctas_per_sm_f64_direct();
   c->kz = choose_kz(nz, gx * gy, c->nsm, pm, !mixed);
   c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
@@ -843,6 +912,7 @@ int glemur_energy(glemur_ctx* c, double* E) {
   DevState hs;
   int rc = read_state(c, &hs);
   if (rc) return rc;
+  if (hs.status == ST_TIMEOUT) return GLEMUR_ERR_TIMEOUT;
   *E = hs.E;
   return GLEMUR_OK;
 }
@@ -858,6 +928,7 @@ int glemur_forcefree_err(glemur_ctx* c, double* xi, double* xi_sin) {
   DevState hs;
   int rc = read_state(c, &hs);
   if (rc) return rc;
+  if (hs.status == ST_TIMEOUT) return GLEMUR_ERR_TIMEOUT;
   *xi = hs.xi;
   *xi_sin = hs.xi_sin;
   return GLEMUR_OK;
@@ -917,6 +988,7 @@ const char* glemur_strerror(int status) {
     case GLEMUR_ERR_DT_UNDERFLOW: return "step size underflow / too many rejections";
     case GLEMUR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case GLEMUR_ERR_TOO_LARGE: return "grid larger than the fixed scratch supports";
+    case GLEMUR_ERR_TIMEOUT: return "a device-side wait for a tile load timed out";
     default: return "unknown status";
   }
 }

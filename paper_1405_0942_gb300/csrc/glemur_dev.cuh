@@ -26,18 +26,33 @@ constexpr int XW = TX + 4, XH = TY + 4, XP = XW * XH;
 constexpr int BW = TX + 2, BH = TY + 2, BP = BW * BH;
 // Displacement tile with a halo of 1 (direct current).
 constexpr int DW = TX + 2, DH = TY + 2, DP = DW * DH;
+// TMA boxes of the mixed-precision mimetic stages (FP32 SoA fields, all
+// three components per box).  A box must start on a 16-byte boundary, so it
+// starts 4 columns left of the tile (2 of them unused) and is YW wide.
+constexpr int YW = TX + 8;            // box width (floats)
+constexpr int YH = TY + 4;            // stage-input box height (halo 2)
+constexpr int YCS = YW * YH;          // floats per component
+constexpr int YPL = 3 * YCS;          // floats per stage-input plane
+constexpr int ZH = TY + 2;            // B0 box height (halo 1)
+constexpr int ZCS = YW * ZH;          // floats per component
+constexpr int ZPL = 3 * ZCS;          // floats per B0 plane
+constexpr int ZSTRIDE = (ZPL * 4 + 127) / 128 * 32;  // B0 slot stride (floats), 128-byte aligned
+constexpr unsigned YBYTES = YPL * 4, ZBYTES = ZPL * 4;
 
 // Error flags raised by the stage kernels: det G <= 0 in the accepted state
 // (stage 1 input: fatal) or in a trial stage input (the attempt is
 // rejected with the largest shrink).
 constexpr unsigned FLAG_COLLAPSED = 1u;
 constexpr unsigned FLAG_FOLDED_TRIAL = 2u;
+// A bounded wait for a tile load gave up (the attempt's results are void).
+constexpr unsigned FLAG_TIMEOUT = 4u;
 
 // Device status codes (same values as glemur_status).
 constexpr int ST_OK = 0;
 constexpr int ST_COLLAPSED = -3;
 constexpr int ST_NONFINITE = -4;
 constexpr int ST_DT_UNDERFLOW = -5;
+constexpr int ST_TIMEOUT = -8;
 
 // Control state of the time integration, resident in the workspace.  The
 // step-control kernel updates it after every attempt, so the host never has

@@ -11,4 +11,15 @@ cudaError_t prepare_f32_mimetic() { return prepare_stage_t<float, float, 0, 3>()
 
 int ctas_per_sm_f32_mimetic() { return stage_ctas_per_sm_t<float, float, 0, 3>(); }
 
+// The same stages with the stage input and B0 loaded as TMA tiles (nx a
+// multiple of 4).
+cudaError_t launch_f32_mimetic_tma(const StageArgs<float>& a, const TmaMaps& maps, int stage,
+                                   dim3 grid, cudaStream_t s) {
+  return launch_stage_tma_t<3>(a, maps, stage, grid, s);
+}
+
+cudaError_t prepare_f32_mimetic_tma() { return prepare_stage_tma_t<3>(); }
+
+int ctas_per_sm_f32_mimetic_tma() { return stage_tma_ctas_per_sm_t<3>(); }
+
 }  // namespace glemur

@@ -1,7 +1,12 @@
 """Golden fixture tests/golden/tube16_relax.json (written by
 tests/golden/make_golden.py from the oracle only): the oracle must keep
-reproducing it exactly, and the GPU library must match it within the FP64
-parity tolerances without running the oracle."""
+reproducing it, and the GPU library must match it within the FP64 parity
+tolerances without running the oracle.
+
+The oracle's own check allows last-bit differences: the seeded inputs go
+through numpy's exp and sin, whose results may differ by an ulp between CPU
+architectures, and the step-size law dt' = dt (Lambda0/Lambda)^0.2 passes on
+the relative rounding of the small error norm Lambda."""
 import json
 import os
 
@@ -24,11 +29,12 @@ def test_oracle_reproduces_golden():
     w = gi.make_workload("tube", n=16)
     x, dt_next, log, st, rc = ora.relax(w.grid, w.x0, w.B0, gold["steps"], gold["dt0"])
     assert rc == ora.OK
-    assert list(log) == gold["accepted_dt"] and st["rejected"] == gold["rejected"]
-    assert ora.energy(w.grid, x, w.B0)[0] == gold["energy"]
+    assert st["rejected"] == gold["rejected"] and len(log) == len(gold["accepted_dt"])
+    assert np.allclose(log, gold["accepted_dt"], rtol=1e-9, atol=0)
+    assert abs(ora.energy(w.grid, x, w.B0)[0] - gold["energy"]) <= 1e-13 * gold["energy"]
     for s in gold["samples"]:
         i, j, k = s["ijk"]
-        assert [x[c, k, j, i] for c in range(3)] == s["x"]
+        assert np.abs(x[:, k, j, i] - np.array(s["x"])).max() <= 1e-12
 
 
 @pytest.mark.gpu

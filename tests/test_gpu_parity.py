@@ -77,6 +77,33 @@ def test_velocity_mixed(G, dims, curl):
     assert rel_inf(u, u_ref) < 2e-4
 
 
+@pytest.mark.parametrize("tma", ["1", "0"], ids=["tma", "registers"])
+@pytest.mark.parametrize("dims", [(44, 19, 23), (64, 12, 9)], ids=lambda d: "x".join(map(str, d)))
+def test_mixed_tile_paths(G, dims, tma, monkeypatch):
+    """nx a multiple of 4 (and at least one 40 x 12 box): the mixed mimetic
+    stages load their tiles by TMA; GLEMUR_TMA=0 selects the register-staged
+    loads.  Both against the oracle: the stage-1 velocity and one full
+    Cash-Karp step (all six stages), ragged tiles in x, y and z."""
+    monkeypatch.setenv("GLEMUR_TMA", tma)
+    g, x0, B0 = braid_case(*dims)
+    X = gi.nodes(g)
+    r = relaxation(G, g, x0, B0, precision=1)
+    u = r.velocity().cpu().numpy()
+    u_ref, _ = ora.velocity(g, x0, B0, 0)
+    assert rel_inf(u, u_ref) < 2e-4
+    dt = 2e-3
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, 0)
+    assert rc == ora.OK
+    st = r.step_fixed(dt)
+    x = r.get_x().cpu().numpy()
+    step = np.abs(x_ref - x0).max()
+    assert np.abs(x - x_ref).max() <= 3e-4 * step + 2e-7 * np.abs(x_ref - X).max()
+    assert abs(st["lam"] - lam_ref) <= 5e-2 * lam_ref
+    # energy (stage-1 diagnostics of the tile kernels) against the oracle
+    E_ref, _ = ora.energy(g, x_ref, B0)
+    assert abs(r.energy() - E_ref) <= 1e-6 * E_ref
+
+
 def test_positions_round_trip(G):
     g, x0, B0 = braid_case(20, 11, 9)
     for prec, tol in ((0, 0.0), (1, 1e-8)):
@@ -126,6 +153,24 @@ def test_one_step_mixed(G, dims, curl):
     assert err <= 3e-4 * step + 2e-7 * np.abs(x_ref - X).max(), (err, step)
     # the error norm is a cancelling combination of the k_j: 5 % relative
     assert abs(st["lam"] - lam_ref) <= 5e-2 * lam_ref, (st["lam"], lam_ref)
+
+
+def test_fused_fp64_stages(G, monkeypatch):
+    """GLEMUR_F64_FUSED=1 selects the single-kernel FP64 mimetic stages
+    (halo recomputation) instead of the two-pass ones: the same parity
+    targets (velocity 1e-11 of its max-norm, one step 1e-12 relative)."""
+    monkeypatch.setenv("GLEMUR_F64_FUSED", "1")
+    g, x0, B0 = braid_case(37, 19, 23)
+    r = relaxation(G, g, x0, B0)
+    u_ref, _ = ora.velocity(g, x0, B0, 0)
+    assert rel_inf(r.velocity().cpu().numpy(), u_ref) < 1e-11
+    dt = 2e-3
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, 0)
+    st = r.step_fixed(dt)
+    assert rel_inf(r.get_x().cpu().numpy(), x_ref) < 1e-12
+    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref
+    E_ref, _ = ora.energy(g, x_ref, B0)
+    assert abs(r.energy() - E_ref) <= 1e-13 * E_ref
 
 
 def test_hundred_steps_replayed_schedule_fp64(G):
