@@ -191,6 +191,7 @@ struct Acc;
 template <>
 struct Acc<double> {
   double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
+  int bad = 0;
   __device__ __forceinline__ void add_e(double w) { e += w; }
   __device__ __forceinline__ void max_lam(double v) { lam = nanmax(lam, v); }
   __device__ __forceinline__ double e_total() const { return e; }
@@ -198,6 +199,7 @@ struct Acc<double> {
 template <>
 struct Acc<float> {
   float eh = 0.0f, el = 0.0f, lam = 0.0f, xi2 = 0.0f, xis2 = 0.0f;
+  int bad = 0;
   __device__ __forceinline__ void add_e(float w) {
     float s, err;
     two_sum(eh, w, s, err);
@@ -732,21 +734,34 @@ __device__ __forceinline__ void yside(const float* p0, int i0, const float* p1, 
     o[c] = sgn * ((4.0f * p1[i1 + c * YCS] - 3.0f * p0[i0 + c * YCS]) - p2[i2 + c * YCS]);
 }
 
+// Shared-memory planes of the ring around plane q: y_s at q-2 .. q+2 and
+// the B plane of q.
+struct RingPlanes {
+  const float* ym2;
+  const float* ym;
+  const float* yq;
+  const float* yp;
+  const float* yp2;
+};
+
+__device__ __forceinline__ RingPlanes ring_planes(const float* yr, int q) {
+  return RingPlanes{yr + xslot(q - 2) * YPL, yr + xslot(q - 1) * YPL, yr + xslot(q) * YPL,
+                    yr + xslot(q + 1) * YPL, yr + xslot(q + 2) * YPL};
+}
+
 // B (and 1/det G) at every node of plane q in the tile + halo 1, from the
-// TMA stage-input ring; B0s from the TMA B0 plane `zp` or, if null, from
-// the registers `b0v`.
+// TMA stage-input ring planes `R` around q, into the B plane `bq`; B0s from
+// the TMA B0 plane `zp` or, if null, from the registers `b0v`.
 __device__ __forceinline__ void compute_B_tma(const StageArgs<float>& a, int q, int k0, int k1,
                                               const BPts& bp, const float* __restrict__ zp,
-                                              const B0Pts<float>& b0v,
-                                              const float* __restrict__ yr,
-                                              V4<float>* __restrict__ bs, bool diag,
+                                              const B0Pts<float>& b0v, const RingPlanes& R,
+                                              V4<float>* __restrict__ bq, bool diag,
                                               Acc<float>& acc) {
-  const float* yq = yr + xslot(q) * YPL;
-  const float* ym = yr + xslot(q - 1) * YPL;
-  const float* yp = yr + xslot(q + 1) * YPL;
-  const float* ym2 = yr + xslot(q - 2) * YPL;
-  const float* yp2 = yr + xslot(q + 2) * YPL;
-  V4<float>* bq = bs + bslot(q) * BP;
+  const float* yq = R.yq;
+  const float* ym = R.ym;
+  const float* yp = R.yp;
+  const float* ym2 = R.ym2;
+  const float* yp2 = R.yp2;
   const float h20 = a.h2f[0], h21 = a.h2f[1], h22 = a.h2f[2];
   const int sz = q == 0 ? 1 : (q == a.nz - 1 ? 2 : 0);
   const bool own_plane = diag && q >= k0 && q < k1;
@@ -780,8 +795,7 @@ __device__ __forceinline__ void compute_B_tma(const StageArgs<float>& a, int q, 
     g[1][1] += h21;
     g[2][2] += h22;
     const float det = det3(g[0], g[1], g[2]);
-    if (det <= 0.0f)  // NaN: reported by the error norm
-      atomicOr(&a.st->flags, a.stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+    acc.bad |= det <= 0.0f;  // NaN: reported by the error norm
     const float r = recip(det);
     float b0, b1, b2;
     if (zp) {
@@ -806,23 +820,22 @@ __device__ __forceinline__ void compute_B_tma(const StageArgs<float>& a, int q, 
   }
 }
 
-// Mimetic current and velocity at the thread's node of plane m (TMA ring).
+// Mimetic current and velocity at the thread's node of plane m: y_s planes
+// m-1, m, m+1 (ym, yq, yp) and B planes (bm, bq, bp).
 template <int S>
-__device__ __forceinline__ void mimetic_out_tma(const StageArgs<float>& a, int m, int n,
-                                                const float* __restrict__ yr,
-                                                const V4<float>* __restrict__ bs,
+__device__ __forceinline__ void mimetic_out_tma(const StageArgs<float>& a, int n,
+                                                const float* __restrict__ ym,
+                                                const float* __restrict__ yq,
+                                                const float* __restrict__ yp,
+                                                const V4<float>* __restrict__ bm,
+                                                const V4<float>* __restrict__ bq,
+                                                const V4<float>* __restrict__ bp,
                                                 const Centre<float, float, S>& ce, float* dout,
                                                 const float* an, const DevState* st, bool diag,
                                                 Acc<float>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int x0 = (ty + 2) * YW + (tx + 4);
   const int b0i = (ty + 1) * BW + (tx + 1);
-  const float* yq = yr + xslot(m) * YPL;
-  const float* ym = yr + xslot(m - 1) * YPL;
-  const float* yp = yr + xslot(m + 1) * YPL;
-  const V4<float>* bq = bs + bslot(m) * BP;
-  const V4<float>* bm = bs + bslot(m - 1) * BP;
-  const V4<float>* bp = bs + bslot(m + 1) * BP;
   float g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
   ysub(yq, x0 + 1, yq, x0 - 1, g0);
   ysub(yq, x0 + YW, yq, x0 - YW, g1);
@@ -913,17 +926,32 @@ __global__ void __launch_bounds__(NT, MINB)
     if (q >= 0 && q < a.nz && q <= k1) {
       B0Pts<float> b0v;
       load_B0(a, q, bp, b0v);
-      compute_B_tma(a, q, k0, k1, bp, nullptr, b0v, yr, bs, diag, acc);
+      compute_B_tma(a, q, k0, k1, bp, nullptr, b0v, ring_planes(yr, q), bs + bslot(q) * BP, diag,
+                    acc);
     }
   __syncthreads();
+  // ring slots of plane m (y_s: 6, B: 4), advanced without divisions
+  int ys0 = xslot(k0), bs0 = bslot(k0);
   for (int m = k0; m < k1; ++m) {
     const int it = m - k0;
+    // y_s planes m-1 .. m+4 and B planes m-1 .. m+2
+    const float* yl[6];
+#pragma unroll
+    for (int dd = 0; dd < 6; ++dd) {
+      int sl = ys0 + dd - 1;
+      sl += sl < 0 ? XRING : 0;
+      sl -= sl >= XRING ? XRING : 0;
+      yl[dd] = yr + sl * YPL;
+    }
+    V4<float>* bl[4];
+#pragma unroll
+    for (int dd = 0; dd < 4; ++dd) bl[dd] = bs + ((bs0 + dd + BRING - 1) & (BRING - 1)) * BP;
     if (threadIdx.x == 0) {
       const bool ly = m + 4 < a.nz && m + 4 <= k1 + 1;
       const bool lz = m + 3 < a.nz && m + 3 <= k1;
       uint64_t* bar = &bars[it & 1];
       mbar_arrive_expect_tx(bar, (ly ? YBYTES : 0u) + (lz ? ZBYTES : 0u));
-      if (ly) tma_load_4d(yr + xslot(m + 4) * YPL, ymap, i0 - 4, j0 - 2, m + 4, 0, bar);
+      if (ly) tma_load_4d(const_cast<float*>(yl[5]), ymap, i0 - 4, j0 - 2, m + 4, 0, bar);
       if (lz) tma_load_4d(zr + ((m + 3) & 1) * ZSTRIDE, &maps.b0, i0 - 4, j0 - 1, m + 3, 0, bar);
     }
     const bool out = out_xy && m >= 1 && m <= a.nz - 2;
@@ -945,11 +973,18 @@ __global__ void __launch_bounds__(NT, MINB)
     const int qb = m + 2;  // B plane computed in this iteration
     if (qb < a.nz && qb <= k1) {
       B0Pts<float> unused;
-      compute_B_tma(a, qb, k0, k1, bp, zr + (qb & 1) * ZSTRIDE, unused, yr, bs, diag, acc);
+      const RingPlanes R{yl[1], yl[2], yl[3], yl[4], yl[5]};  // planes m .. m+4
+      compute_B_tma(a, qb, k0, k1, bp, zr + (qb & 1) * ZSTRIDE, unused, R, bl[3], diag, acc);
     }
-    if (out) mimetic_out_tma<S>(a, m, n, yr, bs, ce, dout, an, st, diag, acc);
+    if (out)
+      mimetic_out_tma<S>(a, n, yl[0], yl[1], yl[2], bl[0], bl[1], bl[2], ce, dout, an, st, diag,
+                         acc);
+    ys0 = ys0 == XRING - 1 ? 0 : ys0 + 1;
+    bs0 = (bs0 + 1) & (BRING - 1);
     __syncthreads();
   }
+  if (__syncthreads_or(acc.bad) && threadIdx.x == 0)
+    atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   write_partials<float, float>(a, FINAL, diag, acc, red);
 }
 
