@@ -48,8 +48,8 @@ L2_FLUSH_BYTES = 512 << 20
 # by (n, precision, curl); absent workloads report null
 NCU_TRAFFIC = {
     (64, "fp64", "mimetic"): 45.86e6,
-    (64, "mixed", "mimetic"): 15.74e6,
-    (128, "mixed", "mimetic"): 154.07e6,
+    (64, "mixed", "mimetic"): 15.71e6,
+    (128, "mixed", "mimetic"): 152.92e6,
 }
 
 

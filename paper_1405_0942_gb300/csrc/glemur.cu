@@ -321,6 +321,7 @@ struct glemur_ctx {
   DevState* st;
   int split;                             // FP64 mimetic stages in two passes
   int tma;                               // mixed mimetic stages with TMA tiles
+  unsigned tma_test_extra;               // test hook: unsatisfiable tile wait
   TmaMaps maps;                          // their tensor maps
   void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
@@ -433,6 +434,7 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
+  a.tma_test_extra = c->tma_test_extra;
   return a;
 }
 
@@ -728,6 +730,11 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   const bool mixed = o.precision == GLEMUR_MIXED;
   if (e == cudaSuccess) e = mixed ? prepare_f32_mimetic() : prepare_f64_mimetic();
   c->tma = 0;
+  // GLEMUR_TEST_TMA_TIMEOUT=1 makes every TMA prologue wait for 16 bytes that
+  // never arrive, so that tests can exercise the bounded wait and the
+  // GLEMUR_ERR_TIMEOUT status without any fault
+  const char* tt = getenv("GLEMUR_TEST_TMA_TIMEOUT");
+  c->tma_test_extra = tt && atoi(tt) > 0 ? 16u : 0u;
   if (e == cudaSuccess && setup_tma(c)) {
     e = prepare_f32_mimetic_tma();
     c->tma = 1;

@@ -103,6 +103,9 @@ struct StageArgs {
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;
+  // bytes the TMA prologue waits for beyond its loads: 0, or > 0 only to
+  // test the bounded wait (the wait then gives up and the attempt fails)
+  unsigned tma_test_extra;
 };
 
 __device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {

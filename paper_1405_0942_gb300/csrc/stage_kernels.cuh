@@ -908,17 +908,17 @@ __global__ void __launch_bounds__(NT, MINB)
       if (q >= 0 && q < a.nz && q <= k1 + 1) bytes += YBYTES;
     const bool z2 = k0 + 2 < a.nz && k0 + 2 <= k1;
     if (z2) bytes += ZBYTES;
-    mbar_arrive_expect_tx(&bars[2], bytes);
+    mbar_arrive_expect_tx(&bars[2], bytes + a.tma_test_extra);
     for (int q = k0 - 2; q <= k0 + 3; ++q)
       if (q >= 0 && q < a.nz && q <= k1 + 1)
         tma_load_4d(yr + xslot(q) * YPL, ymap, i0 - 4, j0 - 2, q, 0, &bars[2]);
     if (z2) tma_load_4d(zr + ((k0 + 2) & 1) * ZSTRIDE, &maps.b0, i0 - 4, j0 - 1, k0 + 2, 0, &bars[2]);
   }
   __syncthreads();
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[2], 0, TMA_WAIT_LIMIT))) {
+  if (__syncthreads_or(!mbar_wait_bounded(&bars[2], 0))) {
     if (threadIdx.x == 0) {
       atomicOr(&a.st->flags, FLAG_TIMEOUT);
-      mbar_wait_bounded(&bars[2], 0, TMA_WAIT_LIMIT);  // boxes still in flight
+      mbar_wait_bounded(&bars[2], 0);  // boxes still in flight
     }
     return;
   }
@@ -960,12 +960,12 @@ __global__ void __launch_bounds__(NT, MINB)
     if (out) ce.issue(a, d, N, n);
     if (it > 0) {
       const int pi = it - 1;
-      const bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1, TMA_WAIT_LIMIT);
+      const bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           atomicOr(&a.st->flags, FLAG_TIMEOUT);
           // let this iteration's boxes land before the CTA leaves
-          mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, TMA_WAIT_LIMIT);
+          mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1);
         }
         return;
       }

@@ -61,17 +61,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait for the phase of the given parity to complete; false if it has not
-// after `limit` polls (each poll blocks for a short hardware interval).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
-  for (int i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
 }
 
-// Polls before a tile wait gives up (each blocks for a short hardware
-// interval; a completed load is seen within the first few).
-constexpr int TMA_WAIT_LIMIT = 1 << 20;
+// A tile wait gives up after this long (a completed load is seen within
+// microseconds).
+constexpr uint64_t TMA_WAIT_NS = 500000000ull;
+
+// Wait for the phase of the given parity to complete; false if it has not
+// after TMA_WAIT_NS nanoseconds of polling.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (int i = 0; i < (1 << 26); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > TMA_WAIT_NS) return false;
+  }
+  return false;
+}
 
 // 4-D tile load: box at coordinates (c0, c1, c2, c3) of `map` into `dst`
 // (128-byte aligned shared memory), completing on `bar`.  c0 times the

@@ -18,7 +18,7 @@ from . import build as _build
 
 OK = 0
 ERR = {-1: "BADARG", -2: "CUDA", -3: "COLLAPSED", -4: "NONFINITE", -5: "DT_UNDERFLOW",
-       -6: "WORKSPACE", -7: "TOO_LARGE"}
+       -6: "WORKSPACE", -7: "TOO_LARGE", -8: "TIMEOUT"}
 FP64, MIXED = 0, 1
 MIMETIC, DIRECT = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
