@@ -236,6 +236,51 @@ def roofline_entry(ms, w, precision, curl, hbm_peak, peak_kind):
     return hbm
 
 
+# bytes per interior node-stage a fused FP64 stage VJP must move: read the
+# stage input, B0 and the adjoint of k_s, write the adjoint of the stage
+# input, read and write the B0 adjoint (6 FP64 vectors)
+ADJ_ALGO_BYTES = 6 * 24.0
+
+
+def adjoint_measure(G, torch, w, precision, steps, flush, hbm_peak, peak_kind):
+    """One reverse step of the relaxation (glemur_vjp_step: recompute of the
+    six stages at x_n, the reverse Runge-Kutta combine and six stage VJPs)
+    per timed iteration, CUDA events on the library's stream, L2 flushed
+    between iterations."""
+    g = w.grid
+    r = G.Relaxation(g.nx, g.ny, g.nz, g.lo, g.hi,
+                     precision=G.MIXED if precision == "mixed" else G.FP64)
+    r.set_x(torch.from_numpy(w.x0).cuda())
+    r.set_B0(torch.from_numpy(w.B0).cuda())
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    lam_next = torch.randn((3, g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda",
+                           generator=gen)
+    lam = torch.empty_like(lam_next)
+    mu = torch.zeros_like(lam_next)
+    dt = 1e-3
+    for _ in range(2):
+        r.vjp_step(dt, lam_next, lam, mu)
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(r.stream)
+        r.vjp_step(dt, lam_next, lam, mu)
+        e1.record(r.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    I = g.n_interior
+    gbs = ADJ_ALGO_BYTES * I * 6 / (ms * 1e-3) / 1e9
+    return {"value": I * 6 / (ms * 1e-3), "unit": "node-stage VJPs/s", "ms_per_step": ms,
+            "precision": precision,
+            "step": "glemur_vjp_step: six-stage recompute + reverse combine + six stage VJPs",
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_node_stage": ADJ_ALGO_BYTES}}
+
+
 def e2e_measure(G, torch, w, precision, curl, steps):
     """Same step through the C ABI with host buffers: H2D of x and B0 from
     pinned memory, the attempt, D2H of the new positions, per step."""
@@ -309,6 +354,10 @@ def our_arm(args):
                 "roofline": roofline_entry(ms2, w, prec, curl, hbm_peak, peak_kind)}
     e2e = None if args.lean else e2e_measure(G, torch, w, args.precision, args.curl,
                                              max(3, min(args.steps, 10)))
+    adj = None
+    if rank == 0 and ws == 1 and not args.lean and args.curl == "mimetic":
+        adj = adjoint_measure(G, torch, w, args.precision, max(3, min(args.steps, 10)), flush,
+                              hbm_peak, peak_kind)
     if ws > 1:
         torch.distributed.barrier()
     if rank != 0:
@@ -327,7 +376,23 @@ def our_arm(args):
         "kernel_ms": {"stages": per_kernel[:6], "control": per_kernel[6]},
         "attempts": {"accepted": st["accepted"], "rejected": st["rejected"]},
         "compare": extra,
+        "adjoint": adj,
     }
+    print(json.dumps(out), flush=True)
+
+
+def adjoint_arm(args):
+    import torch
+    import paper_1405_0942_gb300 as G
+    G.lib()
+    hbm_peak, peak_kind = load_peaks()
+    w = workload(args.workload)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    adj = adjoint_measure(G, torch, w, args.precision, args.steps, flush, hbm_peak, peak_kind)
+    out = {"metric": "node-stage VJPs/s", "value": adj["value"], "unit": adj["unit"],
+           "n_gpus": 1, "steps": args.steps, "warmup": 2, "ms_per_step": adj["ms_per_step"],
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(args, w), "roofline": adj["roofline"]}
     print(json.dumps(out), flush=True)
 
 
@@ -341,6 +406,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--curl", default="mimetic", choices=["mimetic", "direct"])
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the reverse step (glemur_vjp_step) and print its line")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no comparisons, e2e or CPU baseline (profiling)")
     args = ap.parse_args()
@@ -348,6 +415,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.adjoint_only:
+        adjoint_arm(args)
     else:
         our_arm(args)
 
