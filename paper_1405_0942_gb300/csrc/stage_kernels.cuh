@@ -239,61 +239,31 @@ struct LoadPts {
   }
 };
 
-// Global values of plane q needed for its stage input (d and k_1..k_S at the
-// thread's points), held in registers between issue and commit.
-template <typename T, typename C, int S, int LP>
-struct PlaneRaw {
-  C v[LP][3][S + 1];
-
-  __device__ __forceinline__ void issue(const StageArgs<T>& a, const T* __restrict__ d,
-                                        const int* off, int q) {
-    const int N = a.nx * a.ny * a.nz;
-    const int base = q * a.nx * a.ny;
+// One plane of the stage input y at the thread's points of a halo-1 tile,
+// held in registers between issue and commit, stored as three scalar planes
+// (component-major, pitch PITCH) for the direct current.
+template <typename T, typename C, int LP>
+struct PlaneSoA {
+  C v[LP][3];
+  __device__ __forceinline__ void issue(const T* __restrict__ y, int N, int nxy, const int* off,
+                                        int q) {
+    const int base = q * nxy;
 #pragma unroll
     for (int t = 0; t < LP; ++t) {
       if (off[t] < 0) continue;
       const int n = base + off[t];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        v[t][c][0] = (C)__ldg(&d[c * N + n]);
-#pragma unroll
-        for (int j = 0; j < S; ++j) v[t][c][j + 1] = (C)__ldg(&a.k[j][c * N + n]);
-      }
+      for (int c = 0; c < 3; ++c) v[t][c] = (C)__ldg(&y[c * N + n]);
     }
   }
-
-  // d_s = d + sum_j (dt a_sj) k_j into the shared-memory plane `dst`.
   template <int PITCH>
-  __device__ __forceinline__ void commit(const C* ca, const int* off, C* __restrict__ dst) const {
+  __device__ __forceinline__ void commit(const int* off, C* __restrict__ dst) const {
 #pragma unroll
     for (int t = 0; t < LP; ++t) {
       if (off[t] < 0) continue;
       const int p = threadIdx.x + t * NT;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        C s = v[t][c][0];
-#pragma unroll
-        for (int j = 0; j < S; ++j) s = fma(ca[j], v[t][c][j + 1], s);
-        dst[c * PITCH + p] = s;
-      }
-    }
-  }
-
-  // The same, into an array of (x, y, z, pad) points.
-  __device__ __forceinline__ void commit_aos(const C* ca, const int* off, V4<C>* __restrict__ dst) const {
-#pragma unroll
-    for (int t = 0; t < LP; ++t) {
-      if (off[t] < 0) continue;
-      const int p = threadIdx.x + t * NT;
-      C s3[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        C s = v[t][c][0];
-#pragma unroll
-        for (int j = 0; j < S; ++j) s = fma(ca[j], v[t][c][j + 1], s);
-        s3[c] = s;
-      }
-      dst[p] = V4<C>{s3[0], s3[1], s3[2], (C)0};
+      for (int c = 0; c < 3; ++c) dst[c * PITCH + p] = v[t][c];
     }
   }
 };
@@ -477,50 +447,6 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
       const int nb = ((code >> 5) & 3) + (sz != 0);
       const C zeta = nb == 0 ? (C)1 : nb == 1 ? (C)0.5 : nb == 2 ? (C)0.25 : (C)0.125;
       acc.add_e(zeta * dot3(B, B) * det);
-    }
-  }
-}
-
-// Stage output at a node: write k_s, or (last stage) the update and error.
-template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void emit(const StageArgs<T>& a, int stage, int n, const C u[3],
-                                     const C J[3], const C B[3], const T* __restrict__ d,
-                                     T* __restrict__ dout, const DevState* st, bool diag,
-                                     Acc<C>& acc) {
-  const int N = a.nx * a.ny * a.nz;
-  if (diag) {
-    const C u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
-    // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
-    if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
-    const C jb = j2 * b2;
-    if (jb > (C)0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
-  }
-  if (!FINAL) {
-    T* ko = a.k[stage];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ko[c * N + n] = (T)u[c];
-  } else {
-    // fifth-order update (b_2 = b_5 = 0) and embedded error (b_2 - b*_2 = 0)
-    const C b0 = coef_b<C>(st, 0), b2 = coef_b<C>(st, 2), b3 = coef_b<C>(st, 3),
-            b5 = coef_b<C>(st, 5);
-    const C e0 = coef_e<C>(st, 0), e2 = coef_e<C>(st, 2), e3 = coef_e<C>(st, 3),
-            e4 = coef_e<C>(st, 4), e5 = coef_e<C>(st, 5);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const C k1 = (C)__ldg(&a.k[0][c * N + n]), k3 = (C)__ldg(&a.k[2][c * N + n]),
-              k4 = (C)__ldg(&a.k[3][c * N + n]), k5 = (C)__ldg(&a.k[4][c * N + n]);
-      C up = b0 * k1;
-      up = fma(b2, k3, up);
-      up = fma(b3, k4, up);
-      up = fma(b5, u[c], up);
-      C er = e0 * k1;
-      er = fma(e2, k3, er);
-      er = fma(e3, k4, er);
-      er = fma(e4, k5, er);
-      er = fma(e5, u[c], er);
-      dout[c * N + n] = (T)((C)__ldg(&d[c * N + n]) + up);
-      acc.max_lam(fabs(er));
-      if (a.k6) a.k6[c * N + n] = (T)u[c];
     }
   }
 }
@@ -990,19 +916,17 @@ __global__ void __launch_bounds__(NT, MINB)
 
 // ------------------------------------------------------------ direct
 
-template <typename T, typename C, bool FINAL>
-__device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int m, int i0,
-                                           int j0, const C* __restrict__ xs, const T* d,
-                                           T* dout, const DevState* st, bool diag,
-                                           Acc<C>& acc) {
+// Direct current and velocity at the thread's node n (interior) of a plane:
+// stage-input planes below, at and above it (xm, xq, xp; [3][DP] each).
+template <typename T, typename C, int S>
+__device__ __forceinline__ void direct_out(const StageArgs<T>& a, int n,
+                                           const C* __restrict__ xm, const C* __restrict__ xq,
+                                           const C* __restrict__ xp,
+                                           const Centre<T, C, S>& ce, T* dout, const C* an,
+                                           const DevState* st, bool diag, Acc<C>& acc) {
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gi = i0 + tx, gj = j0 + ty;
-  if (gi < 1 || gi > a.nx - 2 || gj < 1 || gj > a.ny - 2 || m < 1 || m > a.nz - 2) return;
   const int N = a.nx * a.ny * a.nz;
   const int p0 = (ty + 1) * DW + (tx + 1);
-  const C* xq = xs + (m % 3) * 3 * DP;
-  const C* xm = xs + ((m + 2) % 3) * 3 * DP;
-  const C* xp = xs + ((m + 1) % 3) * 3 * DP;
   // columns g_a of G and the second differences S_ac = S_ca (index space)
   C g[3][3], Sd[3][3][3];
 #pragma unroll
@@ -1028,7 +952,6 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int
   g[1][1] += h2of<T, C>(a, 1);
   g[2][2] += h2of<T, C>(a, 2);
   // B0s at the node and its differences D_c B0s = B0s(+e_c) - B0s(-e_c)
-  const int n = (m * a.ny + gj) * a.nx + gi;
   const int sx = 1, sy = a.nx, sz = a.nx * a.ny;
   C b[3], Db[3][3];
 #pragma unroll
@@ -1050,7 +973,7 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int
   }
   const C det = det3(g[0], g[1], g[2]);
   if (det <= (C)0)  // NaN: reported by the error norm
-    atomicOr(&a.st->flags, stage == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+    atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   const C r = recip(det);
   C V[3];
 #pragma unroll
@@ -1089,10 +1012,14 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int stage, int
   u[0] = J[1] * B[2] - J[2] * B[1];
   u[1] = J[2] * B[0] - J[0] * B[2];
   u[2] = J[0] * B[1] - J[1] * B[0];
-  emit<T, C, FINAL>(a, stage, n, u, J, B, d, dout, st, diag, acc);
+  emit_centre<T, C, S>(a, n, u, J, B, ce, dout, an, st, diag, acc);
 }
 
-// Stage S (0..5) of Cash-Karp with the direct current.
+// Stage S (0..5) of Cash-Karp with the direct current.  Like the mimetic
+// kernel, stage s reads only its input y_s on the tile (halo 1) and writes
+// k_s and y_{s+1} pointwise.  Shared memory holds a ring of 4 planes of y_s
+// ([3][DP] each): iteration m evaluates plane m from planes m-1 .. m+1 and
+// loads plane m+2 (issued before, committed after the arithmetic).
 template <typename T, typename C, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a) {
   constexpr bool FINAL = S == 5;
@@ -1100,34 +1027,46 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
-  C* xs = reinterpret_cast<C*>(smem_raw);  // [3 planes][3][DP]
+  C* xs = reinterpret_cast<C*>(smem_raw);  // [4 planes][3][DP]
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
+  const int N = a.nx * a.ny * a.nz, nxy = a.nx * a.ny;
   const int cur = st->cur;
   const T* d = a.d[cur];
   T* dout = const_cast<T*>(a.d[cur ^ 1]);
-  C ca[S > 0 ? S : 1];
+  const T* y = S == 0 ? d : a.ys[S & 1];
+  C an[S < 5 ? S + 1 : 1];  // dt a_{S+1, j}: the next stage input
 #pragma unroll
-  for (int j = 0; j < S; ++j) ca[j] = coef_a<C>(st, S, j);
+  for (int j = 0; j < (S < 5 ? S + 1 : 0); ++j) an[j] = coef_a<C>(st, S + 1, j);
   const bool diag = a.diag != 0;
   Acc<C> acc;
   LoadPts<DW, DH, 1> pts;
   pts.init(i0, j0, a.nx, a.ny);
-  using Raw = PlaneRaw<T, C, S, LoadPts<DW, DH, 1>::LP>;
-  for (int q = k0 - 1; q <= k0; ++q) {
-    if (q < 0) continue;
+  using Raw = PlaneSoA<T, C, LoadPts<DW, DH, 1>::LP>;
+  const int gi = i0 + threadIdx.x % TX, gj = j0 + threadIdx.x / TX;
+  const bool out_xy = gi >= 1 && gi <= a.nx - 2 && gj >= 1 && gj <= a.ny - 2;
+  const int nxy_out = gj * a.nx + gi;
+  for (int q = k0 - 1; q <= k0 + 1; ++q) {
+    if (q < 0 || q >= a.nz || q > k1) continue;
     Raw raw;
-    raw.issue(a, d, pts.off, q);
-    raw.template commit<DP>(ca, pts.off, xs + (q % 3) * 3 * DP);
+    raw.issue(y, N, nxy, pts.off, q);
+    raw.template commit<DP>(pts.off, xs + (q & 3) * 3 * DP);
   }
+  __syncthreads();
   for (int m = k0; m < k1; ++m) {
-    if (m + 1 < a.nz) {
-      Raw raw;
-      raw.issue(a, d, pts.off, m + 1);
-      raw.template commit<DP>(ca, pts.off, xs + ((m + 1) % 3) * 3 * DP);
+    const int ql = m + 2;  // plane loaded in this iteration
+    const bool load = ql < a.nz && ql <= k1;
+    Raw raw;
+    if (load) raw.issue(y, N, nxy, pts.off, ql);
+    const bool out = out_xy && m >= 1 && m <= a.nz - 2;
+    const int n = m * nxy + nxy_out;
+    Centre<T, C, S> ce;
+    if (out) {
+      ce.issue(a, d, N, n);
+      direct_out<T, C, S>(a, n, xs + ((m - 1) & 3) * 3 * DP, xs + (m & 3) * 3 * DP,
+                          xs + ((m + 1) & 3) * 3 * DP, ce, dout, an, st, diag, acc);
     }
-    __syncthreads();
-    direct_out<T, C, FINAL>(a, S, m, i0, j0, xs, d, dout, st, diag, acc);
+    if (load) raw.template commit<DP>(pts.off, xs + (ql & 3) * 3 * DP);
     __syncthreads();
   }
   write_partials<T, C>(a, FINAL, diag, acc, red);
@@ -1178,7 +1117,7 @@ int stage_tma_ctas_per_sm_t() {
 
 inline size_t stage_smem_bytes(int curl, size_t csize) {
   return curl == 0 ? (size_t)(XRING * XP + BRING * BP) * 4 * csize
-                   : (size_t)(3 * 3 * DP) * csize;
+                   : (size_t)(4 * 3 * DP) * csize;
 }
 
 // Launch stage `stage` (0..5) of the current `CURL` (0 mimetic, 1 direct).
