@@ -32,6 +32,7 @@ cudaError_t launch_f32_mimetic_tma(const StageArgs<float>& a, const TmaMaps& map
                                    dim3 grid, cudaStream_t s);
 cudaError_t prepare_f32_mimetic_tma();
 int ctas_per_sm_f32_mimetic_tma();
+int tile_rows_f32_mimetic_tma();
 
 struct SplitArgs {
   int nx, ny, nz;
@@ -593,18 +594,20 @@ bool encode_field_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, voi
 }
 
 // TMA tiles for the mixed mimetic stages: rows 16-byte aligned (nx a
-// multiple of 4) and a grid at least one box wide and high.
+// multiple of 4) and a grid at least one box wide and high (box heights:
+// tile height + 4 for the stage input, + 2 for B0).
 bool setup_tma(glemur_ctx* c) {
-  if (c->o.precision != GLEMUR_MIXED || c->nx % 4 || c->nx < YW || c->ny < YH) return false;
+  const int th = tile_rows_f32_mimetic_tma();
+  if (c->o.precision != GLEMUR_MIXED || c->nx % 4 || c->nx < YW || c->ny < th + 4) return false;
   const char* env = getenv("GLEMUR_TMA");
   if (env && atoi(env) == 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   bool ok = true;
   for (int i = 0; i < 2 && ok; ++i)
-    ok = encode_field_map(enc, &c->maps.d[i], c->dbuf[i], c->nx, c->ny, c->nz, YH) &&
-         encode_field_map(enc, &c->maps.ys[i], c->ys[i], c->nx, c->ny, c->nz, YH);
-  return ok && encode_field_map(enc, &c->maps.b0, c->B0s, c->nx, c->ny, c->nz, ZH);
+    ok = encode_field_map(enc, &c->maps.d[i], c->dbuf[i], c->nx, c->ny, c->nz, th + 4) &&
+         encode_field_map(enc, &c->maps.ys[i], c->ys[i], c->nx, c->ny, c->nz, th + 4);
+  return ok && encode_field_map(enc, &c->maps.b0, c->B0s, c->nx, c->ny, c->nz, th + 2);
 }
 
 }  // namespace
@@ -745,12 +748,16 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
     return GLEMUR_ERR_CUDA;
   }
   const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
-  const int pm = mixed ? (c->tma ? ctas_per_sm_f32_mimetic_tma() : ctas_per_sm_f32_mimetic())
+  // the TMA mimetic tile's height depends on its geometry
+  const int thm = c->tma ? tile_rows_f32_mimetic_tma() : TY;
+  const int gym = (ny + thm - 1) / thm;
+  const int pm = mixed ? (c->tma ? ctas_per_sm_f32_mimetic_tma()
+                                 : ctas_per_sm_f32_mimetic())
                        : ctas_per_sm_f64_mimetic();
   const int pd = mixed ? ctas_per_sm_f32_direct() : ctas_per_sm_f64_direct();
-  c->kz = choose_kz(nz, gx * gy, c->nsm, pm, !mixed);
-  c->grid = dim3(gx, gy, (nz + c->kz - 1) / c->kz);
-  c->nblocks = gx * gy * (int)c->grid.z;
+  c->kz = choose_kz(nz, gx * gym, c->nsm, pm, !mixed);
+  c->grid = dim3(gx, gym, (nz + c->kz - 1) / c->kz);
+  c->nblocks = gx * gym * (int)c->grid.z;
   if (c->split) {
     // one wave of CTAs of 256 threads, each over an equal range of node warps
     const long long need = (c->N + 255) / 256;

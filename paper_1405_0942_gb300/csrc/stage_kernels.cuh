@@ -340,9 +340,6 @@ struct BPts {
       code[t] = sx | (sy << 2) | (own << 4) | (((sx != 0) + (sy != 0)) << 5);
     }
   }
-  // The same points indexed into the TMA stage-input tile (YW wide, first
-  // column 4 left of the tile): x0 = (by + 1) YW + bx + 3.
-  __device__ __forceinline__ void init_tma(int i0, int j0, int nx, int ny);
 };
 
 constexpr int XRING = 6;  // planes of x_s in shared memory
@@ -630,290 +627,6 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
   write_partials<T, C>(a, FINAL, diag, acc, red);
 }
 
-// ------------------------------------------------------------ mimetic, TMA tiles
-
-// Mixed precision with nx a multiple of 4: the stage input and B0 arrive in
-// shared memory as TMA boxes of all three components (SoA per plane; box
-// geometry YW, YH, ZH in glemur_dev.cuh).
-
-__device__ __forceinline__ void BPts::init_tma(int i0, int j0, int nx, int ny) {
-  init(i0, j0, nx, ny);
-#pragma unroll
-  for (int t = 0; t < BPT; ++t) {
-    if (x0[t] < 0) continue;
-    const int p = threadIdx.x + t * NT;
-    const int bx = p % BW, by = p / BW;
-    x0[t] = (by + 1) * YW + bx + 3;
-  }
-}
-
-// o = a - b for points of (possibly different) SoA planes.
-__device__ __forceinline__ void ysub(const float* pa, int ia, const float* pb, int ib, float o[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) o[c] = pa[ia + c * YCS] - pb[ib + c * YCS];
-}
-// one-sided second-order difference sgn (4 p1 - 3 p0 - p2)
-__device__ __forceinline__ void yside(const float* p0, int i0, const float* p1, int i1,
-                                      const float* p2, int i2, float sgn, float o[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    o[c] = sgn * ((4.0f * p1[i1 + c * YCS] - 3.0f * p0[i0 + c * YCS]) - p2[i2 + c * YCS]);
-}
-
-// Shared-memory planes of the ring around plane q: y_s at q-2 .. q+2 and
-// the B plane of q.
-struct RingPlanes {
-  const float* ym2;
-  const float* ym;
-  const float* yq;
-  const float* yp;
-  const float* yp2;
-};
-
-__device__ __forceinline__ RingPlanes ring_planes(const float* yr, int q) {
-  return RingPlanes{yr + xslot(q - 2) * YPL, yr + xslot(q - 1) * YPL, yr + xslot(q) * YPL,
-                    yr + xslot(q + 1) * YPL, yr + xslot(q + 2) * YPL};
-}
-
-// B (and 1/det G) at every node of plane q in the tile + halo 1, from the
-// TMA stage-input ring planes `R` around q, into the B plane `bq`; B0s from
-// the TMA B0 plane `zp` or, if null, from the registers `b0v`.
-__device__ __forceinline__ void compute_B_tma(const StageArgs<float>& a, int q, int k0, int k1,
-                                              const BPts& bp, const float* __restrict__ zp,
-                                              const B0Pts<float>& b0v, const RingPlanes& R,
-                                              V4<float>* __restrict__ bq, bool diag,
-                                              Acc<float>& acc) {
-  const float* yq = R.yq;
-  const float* ym = R.ym;
-  const float* yp = R.yp;
-  const float* ym2 = R.ym2;
-  const float* yp2 = R.yp2;
-  const float h20 = a.h2f[0], h21 = a.h2f[1], h22 = a.h2f[2];
-  const int sz = q == 0 ? 1 : (q == a.nz - 1 ? 2 : 0);
-  const bool own_plane = diag && q >= k0 && q < k1;
-#pragma unroll
-  for (int t = 0; t < BPts::BPT; ++t) {
-    const int x0 = bp.x0[t];
-    if (x0 < 0) continue;
-    const int p = threadIdx.x + t * NT;
-    const int code = bp.code[t];
-    const int sx = code & 3, sy = (code >> 2) & 3;
-    float g[3][3];
-    if (sx == 0)
-      ysub(yq, x0 + 1, yq, x0 - 1, g[0]);
-    else if (sx == 1)
-      yside(yq, x0, yq, x0 + 1, yq, x0 + 2, 1.0f, g[0]);
-    else
-      yside(yq, x0, yq, x0 - 1, yq, x0 - 2, -1.0f, g[0]);
-    if (sy == 0)
-      ysub(yq, x0 + YW, yq, x0 - YW, g[1]);
-    else if (sy == 1)
-      yside(yq, x0, yq, x0 + YW, yq, x0 + 2 * YW, 1.0f, g[1]);
-    else
-      yside(yq, x0, yq, x0 - YW, yq, x0 - 2 * YW, -1.0f, g[1]);
-    if (sz == 0)
-      ysub(yp, x0, ym, x0, g[2]);
-    else if (sz == 1)
-      yside(yq, x0, yp, x0, yp2, x0, 1.0f, g[2]);
-    else
-      yside(yq, x0, ym, x0, ym2, x0, -1.0f, g[2]);
-    g[0][0] += h20;
-    g[1][1] += h21;
-    g[2][2] += h22;
-    const float det = det3(g[0], g[1], g[2]);
-    acc.bad |= det <= 0.0f;  // NaN: reported by the error norm
-    const float r = recip(det);
-    float b0, b1, b2;
-    if (zp) {
-      const int zi = x0 - YW;
-      b0 = zp[zi];
-      b1 = zp[zi + ZCS];
-      b2 = zp[zi + 2 * ZCS];
-    } else {
-      b0 = b0v.v[t][0];
-      b1 = b0v.v[t][1];
-      b2 = b0v.v[t][2];
-    }
-    float B[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) B[c] = (g[0][c] * b0 + g[1][c] * b1 + g[2][c] * b2) * r;
-    bq[p] = V4<float>{B[0], B[1], B[2], r};
-    if (own_plane && (code & 16)) {
-      const int nb = ((code >> 5) & 3) + (sz != 0);
-      const float zeta = nb == 0 ? 1.0f : nb == 1 ? 0.5f : nb == 2 ? 0.25f : 0.125f;
-      acc.add_e(zeta * dot3(B, B) * det);
-    }
-  }
-}
-
-// Mimetic current and velocity at the thread's node of plane m: y_s planes
-// m-1, m, m+1 (ym, yq, yp) and B planes (bm, bq, bp).
-template <int S>
-__device__ __forceinline__ void mimetic_out_tma(const StageArgs<float>& a, int n,
-                                                const float* __restrict__ ym,
-                                                const float* __restrict__ yq,
-                                                const float* __restrict__ yp,
-                                                const V4<float>* __restrict__ bm,
-                                                const V4<float>* __restrict__ bq,
-                                                const V4<float>* __restrict__ bp,
-                                                const Centre<float, float, S>& ce, float* dout,
-                                                const float* an, const DevState* st, bool diag,
-                                                Acc<float>& acc) {
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int x0 = (ty + 2) * YW + (tx + 4);
-  const int b0i = (ty + 1) * BW + (tx + 1);
-  float g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
-  ysub(yq, x0 + 1, yq, x0 - 1, g0);
-  ysub(yq, x0 + YW, yq, x0 - YW, g1);
-  ysub(yp, x0, ym, x0, g2);
-  vsub(bq[b0i + 1], bq[b0i - 1], P0);
-  vsub(bq[b0i + BW], bq[b0i - BW], P1);
-  vsub(bp[b0i], bm[b0i], P2);
-  const V4<float> bc = bq[b0i];
-  const float B[3] = {bc.x, bc.y, bc.z};
-  g0[0] += a.h2f[0];
-  g1[1] += a.h2f[1];
-  g2[2] += a.h2f[2];
-  const float c0 = dot3(P1, g2) - dot3(P2, g1);
-  const float c1 = dot3(P2, g0) - dot3(P0, g2);
-  const float c2 = dot3(P0, g1) - dot3(P1, g0);
-  const float rdet = bc.w;
-  float J[3], u[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * rdet;
-  u[0] = J[1] * B[2] - J[2] * B[1];
-  u[1] = J[2] * B[0] - J[0] * B[2];
-  u[2] = J[0] * B[1] - J[1] * B[0];
-  emit_centre<float, float, S>(a, n, u, J, B, ce, dout, an, st, diag, acc);
-}
-
-// Stage S (0..5) of Cash-Karp with the mimetic current, mixed precision,
-// stage input and B0 through TMA.  Iteration m: thread 0 arms barrier m & 1
-// and issues the boxes of y plane m+4 and B0 plane m+3; every thread waits
-// for the boxes issued in iteration m-1 (y plane m+3, B0 plane m+2), forms B
-// at plane m+2 and the current at plane m.  The prologue's boxes complete
-// on a third barrier.
-template <int S, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
-  constexpr bool FINAL = S == 5;
-  const DevState* st = a.st;
-  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
-  if (st->flags & FLAG_TIMEOUT) return;  // an earlier stage of this attempt gave up
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ double red[NT / 32];
-  __shared__ uint64_t bars[3];
-  unsigned char* base =
-      smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // 128-byte aligned
-  float* yr = reinterpret_cast<float*>(base);                         // [XRING][YPL]
-  V4<float>* bs = reinterpret_cast<V4<float>*>(yr + XRING * YPL);     // [BRING][BP]
-  float* zr = reinterpret_cast<float*>(bs + BRING * BP);              // [2][ZSTRIDE]
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * a.kz, k1 = min(a.nz, k0 + a.kz);
-  const int N = a.nx * a.ny * a.nz, nxy = a.nx * a.ny;
-  const int cur = st->cur;
-  const float* d = a.d[cur];
-  float* dout = const_cast<float*>(a.d[cur ^ 1]);
-  const CUtensorMap* ymap = S == 0 ? &maps.d[cur] : &maps.ys[S & 1];
-  float an[S < 5 ? S + 1 : 1];  // dt a_{S+1, j}: the next stage input
-#pragma unroll
-  for (int j = 0; j < (S < 5 ? S + 1 : 0); ++j) an[j] = coef_a<float>(st, S + 1, j);
-  const bool diag = a.diag != 0;
-  Acc<float> acc;
-  BPts bp;
-  bp.init_tma(i0, j0, a.nx, a.ny);
-  const int gi = i0 + threadIdx.x % TX, gj = j0 + threadIdx.x / TX;
-  const bool out_xy = gi >= 1 && gi <= a.nx - 2 && gj >= 1 && gj <= a.ny - 2;
-  const int nxy_out = gj * a.nx + gi;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
-    fence_barrier_init();
-    // prologue boxes: input planes k0-2 .. k0+3, B0 of plane k0+2
-    unsigned bytes = 0;
-    for (int q = k0 - 2; q <= k0 + 3; ++q)
-      if (q >= 0 && q < a.nz && q <= k1 + 1) bytes += YBYTES;
-    const bool z2 = k0 + 2 < a.nz && k0 + 2 <= k1;
-    if (z2) bytes += ZBYTES;
-    mbar_arrive_expect_tx(&bars[2], bytes + a.tma_test_extra);
-    for (int q = k0 - 2; q <= k0 + 3; ++q)
-      if (q >= 0 && q < a.nz && q <= k1 + 1)
-        tma_load_4d(yr + xslot(q) * YPL, ymap, i0 - 4, j0 - 2, q, 0, &bars[2]);
-    if (z2) tma_load_4d(zr + ((k0 + 2) & 1) * ZSTRIDE, &maps.b0, i0 - 4, j0 - 1, k0 + 2, 0, &bars[2]);
-  }
-  __syncthreads();
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[2], 0))) {
-    if (threadIdx.x == 0) {
-      atomicOr(&a.st->flags, FLAG_TIMEOUT);
-      mbar_wait_bounded(&bars[2], 0);  // boxes still in flight
-    }
-    return;
-  }
-  for (int q = k0 - 1; q <= k0 + 1; ++q)
-    if (q >= 0 && q < a.nz && q <= k1) {
-      B0Pts<float> b0v;
-      load_B0(a, q, bp, b0v);
-      compute_B_tma(a, q, k0, k1, bp, nullptr, b0v, ring_planes(yr, q), bs + bslot(q) * BP, diag,
-                    acc);
-    }
-  __syncthreads();
-  // ring slots of plane m (y_s: 6, B: 4), advanced without divisions
-  int ys0 = xslot(k0), bs0 = bslot(k0);
-  for (int m = k0; m < k1; ++m) {
-    const int it = m - k0;
-    // y_s planes m-1 .. m+4 and B planes m-1 .. m+2
-    const float* yl[6];
-#pragma unroll
-    for (int dd = 0; dd < 6; ++dd) {
-      int sl = ys0 + dd - 1;
-      sl += sl < 0 ? XRING : 0;
-      sl -= sl >= XRING ? XRING : 0;
-      yl[dd] = yr + sl * YPL;
-    }
-    V4<float>* bl[4];
-#pragma unroll
-    for (int dd = 0; dd < 4; ++dd) bl[dd] = bs + ((bs0 + dd + BRING - 1) & (BRING - 1)) * BP;
-    if (threadIdx.x == 0) {
-      const bool ly = m + 4 < a.nz && m + 4 <= k1 + 1;
-      const bool lz = m + 3 < a.nz && m + 3 <= k1;
-      uint64_t* bar = &bars[it & 1];
-      mbar_arrive_expect_tx(bar, (ly ? YBYTES : 0u) + (lz ? ZBYTES : 0u));
-      if (ly) tma_load_4d(const_cast<float*>(yl[5]), ymap, i0 - 4, j0 - 2, m + 4, 0, bar);
-      if (lz) tma_load_4d(zr + ((m + 3) & 1) * ZSTRIDE, &maps.b0, i0 - 4, j0 - 1, m + 3, 0, bar);
-    }
-    const bool out = out_xy && m >= 1 && m <= a.nz - 2;
-    const int n = m * nxy + nxy_out;
-    Centre<float, float, S> ce;
-    if (out) ce.issue(a, d, N, n);
-    if (it > 0) {
-      const int pi = it - 1;
-      const bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
-      if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) {
-          atomicOr(&a.st->flags, FLAG_TIMEOUT);
-          // let this iteration's boxes land before the CTA leaves
-          mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1);
-        }
-        return;
-      }
-    }
-    const int qb = m + 2;  // B plane computed in this iteration
-    if (qb < a.nz && qb <= k1) {
-      B0Pts<float> unused;
-      const RingPlanes R{yl[1], yl[2], yl[3], yl[4], yl[5]};  // planes m .. m+4
-      compute_B_tma(a, qb, k0, k1, bp, zr + (qb & 1) * ZSTRIDE, unused, R, bl[3], diag, acc);
-    }
-    if (out)
-      mimetic_out_tma<S>(a, n, yl[0], yl[1], yl[2], bl[0], bl[1], bl[2], ce, dout, an, st, diag,
-                         acc);
-    ys0 = ys0 == XRING - 1 ? 0 : ys0 + 1;
-    bs0 = (bs0 + 1) & (BRING - 1);
-    __syncthreads();
-  }
-  if (__syncthreads_or(acc.bad) && threadIdx.x == 0)
-    atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
-  write_partials<float, float>(a, FINAL, diag, acc, red);
-}
-
 // ------------------------------------------------------------ direct
 
 // Direct current and velocity at the thread's node n (interior) of a plane:
@@ -1073,47 +786,6 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
 }
 
 // ------------------------------------------------------------ launchers
-
-// Dynamic shared memory of the TMA mimetic kernel (+128 for alignment).
-inline size_t stage_tma_smem_bytes() {
-  return 128 + (size_t)XRING * YPL * 4 + (size_t)BRING * BP * 16 + (size_t)2 * ZSTRIDE * 4;
-}
-
-template <int MINB>
-cudaError_t launch_stage_tma_t(const StageArgs<float>& a, const TmaMaps& maps, int stage,
-                               dim3 grid, cudaStream_t s) {
-  const size_t smem = stage_tma_smem_bytes();
-  switch (stage) {
-    case 0: k_stage_mimetic_tma<0, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    case 1: k_stage_mimetic_tma<1, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    case 2: k_stage_mimetic_tma<2, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    case 3: k_stage_mimetic_tma<3, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    case 4: k_stage_mimetic_tma<4, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    case 5: k_stage_mimetic_tma<5, MINB><<<grid, NT, smem, s>>>(a, maps); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-template <int MINB>
-cudaError_t prepare_stage_tma_t() {
-  const int sm = (int)stage_tma_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_stage_mimetic_tma<0, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_mimetic_tma<1, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_mimetic_tma<2, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_mimetic_tma<3, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_mimetic_tma<4, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_mimetic_tma<5, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  return e;
-}
-
-template <int MINB>
-int stage_tma_ctas_per_sm_t() {
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_mimetic_tma<3, MINB>, NT,
-                                                stage_tma_smem_bytes());
-  return n;
-}
 
 inline size_t stage_smem_bytes(int curl, size_t csize) {
   return curl == 0 ? (size_t)(XRING * XP + BRING * BP) * 4 * csize

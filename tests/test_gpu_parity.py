@@ -78,7 +78,8 @@ def test_velocity_mixed(G, dims, curl):
 
 
 @pytest.mark.parametrize("tma", ["1", "0"], ids=["tma", "registers"])
-@pytest.mark.parametrize("dims", [(44, 19, 23), (64, 12, 9)], ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("dims", [(44, 19, 23), (64, 12, 9), (48, 30, 11)],
+                         ids=lambda d: "x".join(map(str, d)))
 def test_mixed_tile_paths(G, dims, tma, monkeypatch):
     """nx a multiple of 4 (and at least one 40 x 12 box): the mixed mimetic
     stages load their tiles by TMA; GLEMUR_TMA=0 selects the register-staged

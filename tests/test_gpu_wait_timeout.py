@@ -28,7 +28,7 @@ def G():
 
 
 def case():
-    g = gi.Grid(64, 16, 8)
+    g = gi.Grid(64, 20, 8)
     X = gi.nodes(g)
     return g, gi.predistort(X, 2), gi.braid_field(X, gi.braid_regions(6, None, True))
 
