@@ -124,7 +124,21 @@ size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
  * `stream` is a cudaStream_t (or NULL).  `workspace` is caller-owned
  * device memory of ws_bytes >= glemur_workspace_bytes(), 256-byte aligned.
  * The positions start at x = X and B0 = 0; call glemur_set_x/glemur_set_B0.
- * On success *out receives the context.  Errors: BADARG, WORKSPACE, CUDA. */
+ * On success *out receives the context.  Errors: BADARG, WORKSPACE, CUDA.
+ *
+ * Kernel selection happens here, once per context; these environment
+ * variables, read at this call, override it (all results stay within the
+ * same tolerances):
+ *   GLEMUR_TMA=0          mixed precision: register-staged tile loads even
+ *                         where TMA tiles apply (nx a multiple of 4, nx >= 40,
+ *                         ny >= 12)
+ *   GLEMUR_F64_FUSED=1    FP64: single-kernel mimetic stages (halo
+ *                         recomputation) instead of the two-pass stages
+ *   GLEMUR_KZ=k           z-planes per CTA of the stage kernels instead of
+ *                         the cost model's choice
+ *   GLEMUR_TEST_TMA_TIMEOUT=1  test hook: every TMA tile wait expects 16
+ *                         bytes that never arrive, so the bounded wait gives
+ *                         up and steps fail with GLEMUR_ERR_TIMEOUT */
 int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz,
                      const double lo[3], const double hi[3],
                      const glemur_opts* opts, void* stream, void* workspace,
