@@ -177,17 +177,44 @@ def run_oracle_sample(w, max_seconds, max_steps, curl):
                       f"{g.nx}x{g.ny}x{g.nz} workload, single thread"}
 
 
+def _oracle_worker(job):
+    """One host core's share of the all-core oracle sample (spawned process)."""
+    name, max_seconds, curl = job
+    return run_oracle_sample(workload(name), max_seconds, 10 ** 9, curl)
+
+
+def run_oracle_all_cores(name, max_seconds, curl):
+    """The oracle as it stands on every host core: one independent process per
+    core, each relaxing its own copy of the workload for `max_seconds`; the
+    throughput is the sum.  Processes are spawned (never forked from a
+    process that has used the GPU)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_worker, [(name, max_seconds, curl)] * n)
+    value = sum(r["value"] for r in res)
+    steps = sum(r["steps"] for r in res)
+    w = workload(name)
+    g = w.grid
+    return {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+            "seconds": max(r["seconds"] for r in res), "steps": steps,
+            "single_core_value": res[0]["value"],
+            "sample": f"{steps} full FP64 Cash-Karp attempts of the oracle on the "
+                      f"{g.nx}x{g.ny}x{g.nz} workload, {n} independent single-thread "
+                      f"processes (one per host core), about {max_seconds:.0f} s each"}
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     w = workload(args.workload)
-    for _ in range(min(args.warmup, 1)):
-        run_oracle_sample(w, 1e9, 1, args.curl)
-    cb = run_oracle_sample(w, 120.0, args.steps, args.curl)
+    # each core relaxes its own copy for a bounded time: about 4 s per timed
+    # step requested, at most 120 s
+    cb = run_oracle_all_cores(args.workload, min(120.0, 4.0 * max(args.steps, 1)), args.curl)
     out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
            "steps": cb["steps"], "warmup": args.warmup,
-           "ms_per_step": 1e3 * cb["seconds"] / cb["steps"], "higher_is_better": True,
+           "ms_per_step": 1e3 * w.grid.n_interior * 6 / cb["value"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference", "config": config_dict(args, w), "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -362,7 +389,8 @@ def our_arm(args):
         torch.distributed.barrier()
     if rank != 0:
         return
-    cb = run_oracle_sample(w, 12.0, 1000, args.curl) if ws == 1 and not args.lean else None
+    cb = (run_oracle_all_cores(args.workload, 12.0, args.curl)
+          if ws == 1 and not args.lean else None)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms.sum(axis=1).mean(),
