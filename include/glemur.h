@@ -33,7 +33,7 @@
  *
  * Errors.  Every int-returning call returns GLEMUR_OK (0) or a negative
  * GLEMUR_ERR_* code; glemur_strerror() names it.  After an error status
- * from the step (COLLAPSED, NONFINITE, DT_UNDERFLOW) the context keeps the
+ * from the step (COLLAPSED, NONFINITE, DT_UNDERFLOW, TIMEOUT) the context keeps the
  * last accepted state and refuses further steps until glemur_set_x().
  */
 #ifndef GLEMUR_H
