@@ -157,10 +157,46 @@ __global__ void k_diag_finalize(DevState* st, const double* part, int nb) {
   if (threadIdx.x == 0 && (st->flags & FLAG_TIMEOUT)) st->status = ST_TIMEOUT;
 }
 
+// r^0.2 for the step-size law of eq. "time stepping": one Newton step on
+// y^5 = r (Newton's method for the n-th root, y <- ((n-1) y + r / y^(n-1))
+// / n, which converges quadratically) from an FP32 estimate: ~1e-7 -> ~1e-14
+// relative, with a handful of FP64 operations instead of a double pow on
+// GB300's narrow FP64 pipe.  Outside the estimate's float range, pow.
+__device__ double fifth_root(double r) {
+  if (!(r > 1e-30 && r < 1e30)) return pow(r, 0.2);
+  const double y = (double)powf((float)r, 0.2f);
+  const double y2 = y * y;
+  return 0.2 * (4.0 * y + r / (y2 * y2));
+}
+
+// dt-scaled coefficients for step size dt, one entry per thread (the 36
+// a_sj and the 6 b_j, b_j - b*_j; threads >= 42 idle).
+__device__ void set_coeffs_parallel(DevState* st, double dt) {
+  const int t = threadIdx.x;
+  if (t < 36) {
+    const int s = t / 6, j = t % 6;
+    const double v = dt * CK_A[s][j];
+    st->dta[s][j] = v;
+    st->dtaf[s][j] = (float)v;
+  } else if (t < 42) {
+    const int s = t - 36;
+    const double b = dt * CK_B5[s], e = dt * (CK_B5[s] - CK_B4[s]);
+    st->dtb[s] = b;
+    st->dte[s] = e;
+    st->dtbf[s] = (float)b;
+    st->dtef[s] = (float)e;
+  }
+}
+
 // Eq. "time stepping" and the acceptance rule around it, after each attempt.
+// Thread 0 takes the decision from a snapshot of the control state (all
+// loads independent, then all stores); the block then writes the dt-scaled
+// coefficients of the next attempt in parallel.
 __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
   if (st->status != ST_OK || st->n_accept >= st->target) return;
   __shared__ double sh[96];
+  __shared__ double dt_next;
+  __shared__ int go_on;
   double m = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) m = nanmax(m, part[PART_LAMBDA * nb + b]);
   for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -172,76 +208,74 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
   }
   __syncthreads();
   if (diag) finalize_diag(st, part, nb, sh);
-  if (threadIdx.x != 0) return;
-  const double lam = sh[95];
-  const double dt = st->dt;
-  st->lambda = lam;
-  if (st->flags & FLAG_TIMEOUT) {
-    st->status = ST_TIMEOUT;
-    st->n_reject++;
-    return;
-  }
-  if (st->flags & FLAG_COLLAPSED) {
-    st->status = ST_COLLAPSED;
-    st->n_reject++;
-    return;
-  }
-  const bool folded = (st->flags & FLAG_FOLDED_TRIAL) != 0;
-  if (!folded && !isfinite(lam)) {
-    st->status = ST_NONFINITE;
-    st->n_reject++;
-    return;
-  }
-  bool accept;
-  double dtn;
-  if (folded) {
-    // a trial stage folded the grid: reject with the largest shrink
-    accept = false;
-    dtn = dt * st->shrink_min;
-    st->lambda = INFINITY;
-    if (st->consec + 1 > st->max_rejects || dtn < st->dt_min) {
-      st->status = ST_DT_UNDERFLOW;
-      st->n_reject++;
-      st->consec++;
-      return;
+  if (threadIdx.x == 0) {
+    const double lam = sh[95];
+    const double dt = st->dt, lambda0 = st->lambda0, safety = st->safety;
+    const double shrink_min = st->shrink_min, grow_max = st->grow_max, dt_min = st->dt_min;
+    const double t = st->t;
+    const unsigned flags = st->flags;
+    const int replay = st->replay, consec = st->consec, max_rejects = st->max_rejects;
+    const int cur = st->cur;
+    const long long n_acc = st->n_accept, n_rej = st->n_reject;
+    int status = ST_OK;
+    bool accept = false;
+    double dtn = dt;
+    const bool folded = (flags & FLAG_FOLDED_TRIAL) != 0;
+    double lam_out = lam;
+    if (flags & FLAG_TIMEOUT) {
+      status = ST_TIMEOUT;
+    } else if (flags & FLAG_COLLAPSED) {
+      status = ST_COLLAPSED;
+    } else if (!folded && !isfinite(lam)) {
+      status = ST_NONFINITE;
+    } else if (folded) {
+      // a trial stage folded the grid: reject with the largest shrink
+      dtn = dt * shrink_min;
+      lam_out = INFINITY;
+      if (consec + 1 > max_rejects || dtn < dt_min) status = ST_DT_UNDERFLOW;
+    } else if (replay) {
+      accept = true;
+    } else if (lam > lambda0) {
+      double fac = safety * fifth_root(lambda0 / lam);
+      if (fac < shrink_min) fac = shrink_min;
+      dtn = dt * fac;
+      if (consec + 1 > max_rejects || dtn < dt_min) status = ST_DT_UNDERFLOW;
+    } else {
+      accept = true;
+      double fac = 1.0;
+      if (lam < 0.5 * lambda0) {
+        fac = lam > 0.0 ? safety * fifth_root(lambda0 / lam) : grow_max;
+        if (fac > grow_max) fac = grow_max;
+      }
+      dtn = dt * fac;
     }
-  } else if (st->replay) {
-    accept = true;
-    dtn = dt;
-    st->replay = 0;
-  } else if (lam > st->lambda0) {
-    double fac = st->safety * pow(st->lambda0 / lam, 0.2);
-    if (fac < st->shrink_min) fac = st->shrink_min;
-    accept = false;
-    dtn = dt * fac;
-    if (st->consec + 1 > st->max_rejects || dtn < st->dt_min) {
-      st->status = ST_DT_UNDERFLOW;
-      st->n_reject++;
-      st->consec++;
-      return;
+    st->lambda = lam_out;
+    if (status != ST_OK) {
+      // the attempt ends the run: counted as a rejection, state untouched
+      st->status = status;
+      st->n_reject = n_rej + 1;
+      if (status == ST_DT_UNDERFLOW) st->consec = consec + 1;
+      go_on = 0;
+    } else {
+      if (replay) st->replay = 0;
+      if (accept) {
+        st->dt_last = dt;
+        st->t = t + dt;
+        st->cur = cur ^ 1;
+        st->n_accept = n_acc + 1;
+        st->consec = 0;
+      } else {
+        st->n_reject = n_rej + 1;
+        st->consec = consec + 1;
+      }
+      st->dt = dtn;
+      st->flags = 0;
+      dt_next = dtn;
+      go_on = 1;
     }
-  } else {
-    accept = true;
-    double fac = 1.0;
-    if (lam < 0.5 * st->lambda0) {
-      fac = lam > 0.0 ? st->safety * pow(st->lambda0 / lam, 0.2) : st->grow_max;
-      if (fac > st->grow_max) fac = st->grow_max;
-    }
-    dtn = dt * fac;
   }
-  if (accept) {
-    st->dt_last = dt;
-    st->t += dt;
-    st->cur ^= 1;
-    st->n_accept++;
-    st->consec = 0;
-  } else {
-    st->n_reject++;
-    st->consec++;
-  }
-  st->dt = dtn;
-  st->flags = 0;
-  set_coeffs(st);
+  __syncthreads();
+  if (go_on) set_coeffs_parallel(st, dt_next);
 }
 
 // ---- layout conversions at the boundary (float64 SoA fields) ----------

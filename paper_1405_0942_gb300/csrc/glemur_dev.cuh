@@ -112,9 +112,29 @@ __device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {
   return ((long long)k * ny + j) * nx + i;
 }
 
-// max that propagates NaN: the result is NaN if either input is.
+// max of two non-negative doubles that propagates NaN (of either sign),
+// on the integer pipes: the bit patterns of non-negative doubles order like
+// unsigned integers and every NaN pattern lies above +inf.  (All maxima of
+// the step -- error norms, xi^2 -- are of non-negative values; -0 must not
+// occur.)  GB300's FP64 pipe is 1/64 of its FP32 rate, so FP64 compares in
+// reductions and per-node maxima are worth avoiding.
 __device__ __forceinline__ double nanmax(double a, double b) {
-  return (a > b || a != a) ? a : b;
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  return __longlong_as_double((long long)(ua > ub ? ua : ub));
 }
+
+// a > b for non-negative doubles (a NaN a counts as larger), on the integer
+// pipes (see nanmax); the float overload is the plain compare.
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return (unsigned long long)__double_as_longlong(a) > (unsigned long long)__double_as_longlong(b);
+}
+__device__ __forceinline__ bool gt_nonneg(float a, float b) { return a > b || a != a; }
+// not a NaN (integer test for doubles)
+__device__ __forceinline__ bool not_nan(double a) {
+  return ((unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull) <=
+         0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool not_nan(float a) { return a == a; }
 
 }  // namespace glemur

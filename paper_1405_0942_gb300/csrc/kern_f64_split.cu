@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
     u[2] = J[0] * B[1] - J[1] * B[0];
     if (S == 0 && a.diag) {
       const double u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
-      if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
+      if (gt_nonneg(u2, acc.xi2 * b2 * b2)) acc.xi2 = u2 / (b2 * b2);
       const double jb = j2 * b2;
-      if (jb > 0.0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+      if (gt_nonneg(jb, 0.0) && gt_nonneg(u2, acc.xis2 * jb) && not_nan(u2)) acc.xis2 = u2 / jb;
     }
     if (!FINAL) {
 #pragma unroll

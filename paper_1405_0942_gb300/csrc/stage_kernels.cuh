@@ -460,9 +460,9 @@ __device__ __forceinline__ void emit_centre(const StageArgs<T>& a, int n, const 
   if (diag) {
     const C u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
     // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
-    if (u2 > acc.xi2 * b2 * b2 || u2 != u2) acc.xi2 = u2 / (b2 * b2);
+    if (gt_nonneg(u2, acc.xi2 * b2 * b2)) acc.xi2 = u2 / (b2 * b2);
     const C jb = j2 * b2;
-    if (jb > (C)0 && u2 > acc.xis2 * jb) acc.xis2 = u2 / jb;
+    if (gt_nonneg(jb, (C)0) && gt_nonneg(u2, acc.xis2 * jb) && not_nan(u2)) acc.xis2 = u2 / jb;
   }
   if constexpr (S < 5) {
     T* ko = a.k[S];
