@@ -136,5 +136,10 @@ __device__ __forceinline__ bool not_nan(double a) {
          0x7ff0000000000000ull;
 }
 __device__ __forceinline__ bool not_nan(float a) { return a == a; }
+// a <= 0 (false for NaN), integer test for doubles
+__device__ __forceinline__ bool le_zero(double a) {
+  return __double_as_longlong(a) <= 0 && not_nan(a);  // sign bit set, or +0
+}
+__device__ __forceinline__ bool le_zero(float a) { return a <= 0.0f; }
 
 }  // namespace glemur

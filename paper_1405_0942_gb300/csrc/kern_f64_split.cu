@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
     split_gcol(a, y, N, n, 1, j, a.ny, a.nx, g1);
     split_gcol(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
     const double det = det3(g0, g1, g2);
-    if (det <= 0.0)  // NaN: reported by the error norm
+    if (le_zero(det))  // NaN: reported by the error norm
       atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
     const double r = 1.0 / det;
     const double b0 = __ldg(&a.B0s[n]), b1 = __ldg(&a.B0s[N + n]), b2 = __ldg(&a.B0s[2 * N + n]);

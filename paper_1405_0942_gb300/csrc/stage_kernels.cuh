@@ -431,7 +431,7 @@ __device__ __forceinline__ void compute_B(const StageArgs<T>& a, int q, int k0, 
     g[1][1] += h21;
     g[2][2] += h22;
     const C det = det3(g[0], g[1], g[2]);
-    if (det <= (C)0)  // NaN: reported by the error norm
+    if (le_zero(det))  // NaN: reported by the error norm
       atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
     const C r = recip(det);
     const C b0 = b0v.v[t][0], b1 = b0v.v[t][1], b2 = b0v.v[t][2];
@@ -685,7 +685,7 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int n,
     cof[i][2] = g[0][i1] * g[1][i2] - g[1][i1] * g[0][i2];
   }
   const C det = det3(g[0], g[1], g[2]);
-  if (det <= (C)0)  // NaN: reported by the error norm
+  if (le_zero(det))  // NaN: reported by the error norm
     atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   const C r = recip(det);
   C V[3];
