@@ -379,8 +379,19 @@ def our_arm(args):
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.sum(axis=1).mean(),
                 "speedup_vs_primary": v2 / value,
                 "roofline": roofline_entry(ms2, w, prec, curl, hbm_peak, peak_kind)}
-    e2e = None if args.lean else e2e_measure(G, torch, w, args.precision, args.curl,
-                                             max(3, min(args.steps, 10)))
+    e2e = None
+    if not args.lean:
+        # every rank drives its own replica through the C ABI with host
+        # buffers; whole-job throughput = units of all ranks / slowest rank
+        e2e_steps = max(3, min(args.steps, 10))
+        barrier()
+        e2e = e2e_measure(G, torch, w, args.precision, args.curl, e2e_steps)
+        t_e2e, u_e2e = reduce_over_ranks(e2e["ms_per_step"] * 1e-3 * e2e_steps,
+                                         w.grid.n_interior * 6 * e2e_steps, ws, "cuda")
+        e2e["value"] = u_e2e / t_e2e
+        e2e["ms_per_step"] = t_e2e / e2e_steps * 1e3
+        e2e["h2d_bytes_per_step"] *= ws          # all ranks' copies
+        e2e["d2h_bytes_per_step"] *= ws
     adj = None
     if rank == 0 and ws == 1 and not args.lean and args.curl == "mimetic":
         adj = adjoint_measure(G, torch, w, args.precision, max(3, min(args.steps, 10)), flush,
