@@ -47,6 +47,11 @@ def test_host_only_entry_points():
     assert b64 % 256 == 0 and b32 % 256 == 0 and b64 > b32 >= 8 * 3 * n ** 3 * 4
     assert g.workspace_bytes(2, n, n, g.FP64) == 0
     assert g.workspace_bytes(n, n, n, 7) == 0
+    # the largest grid: kernels index 3N components with 32-bit ints
+    assert g.workspace_bytes(894, 894, 894, g.MIXED) > 0          # 3N < 2^31
+    assert g.workspace_bytes(895, 895, 895, g.MIXED) == 0
+    assert g.workspace_bytes(1 << 20, 1 << 20, 3, g.FP64) == 0    # no int overflow
+    assert L.glemur_strerror(-8) == b"a device-side wait for a tile load timed out"
     h = ctypes.c_void_p()
     lo = (ctypes.c_double * 3)(-1, -1, -1)
     hi = (ctypes.c_double * 3)(1, 1, 1)
