@@ -50,11 +50,44 @@ __device__ __forceinline__ void cta_range(int N, int& begin, int& end) {
   end = (int)(w1 * 32 < N ? w1 * 32 : N);
 }
 
-__device__ __forceinline__ void split_nodes(const SplitArgs& a, int n, int& i, int& j, int& k) {
-  i = n % a.nx;
-  const int r = n / a.nx;
-  j = r % a.ny;
-  k = r / a.ny;
+// Interior nodes enumerated densely: t in [0, (nx-2)(ny-2)(nz-2)) -> node.
+// A warp then holds 32 interior nodes, so the interior code (central
+// differences only) runs with no boundary lanes in it.
+__device__ __forceinline__ int interior_node(const SplitArgs& a, int t, int& i, int& j, int& k) {
+  const int nxi = a.nx - 2, nyi = a.ny - 2;
+  i = 1 + t % nxi;
+  const int r = t / nxi;
+  j = 1 + r % nyi;
+  k = 1 + r / nyi;
+  return (k * a.ny + j) * a.nx + i;
+}
+
+// Boundary nodes enumerated densely, face by face: the two z faces (whole
+// planes), the two y faces without their z edges, the two x faces without
+// their y and z edges; b in [0, N - interior).
+__device__ __forceinline__ int boundary_node(const SplitArgs& a, int b, int& i, int& j, int& k) {
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int fz = nx * ny, fy = nx * (nz - 2);
+  if (b < 2 * fz) {
+    k = b < fz ? 0 : nz - 1;
+    const int r = b < fz ? b : b - fz;
+    j = r / nx;
+    i = r - j * nx;
+  } else if (b < 2 * fz + 2 * fy) {
+    int r = b - 2 * fz;
+    j = r < fy ? 0 : ny - 1;
+    r = r < fy ? r : r - fy;
+    k = 1 + r / nx;
+    i = r % nx;
+  } else {
+    const int fx = (ny - 2) * (nz - 2);
+    int r = b - 2 * fz - 2 * fy;
+    i = r < fx ? 0 : nx - 1;
+    r = r < fx ? r : r - fx;
+    k = 1 + r / (ny - 2);
+    j = 1 + r % (ny - 2);
+  }
+  return (k * ny + j) * nx + i;
 }
 
 // Column a of G at node (i, j, k) from the stage input y.
@@ -77,45 +110,81 @@ __device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __r
   out[ax] += a.h2[ax];
 }
 
-// Pass B (stage s): B and 1/det G at every node; in the diagnostic launch
-// also the energy partials (eq. "magnetic energy").
+// B and 1/det G at node n = (i, j, k) from the stage input y (eq. "B
+// transformation"); returns the node's energy term zeta |B|^2 det G if
+// `energy`.  FACE: the general stencil (one-sided differences on the
+// boundary faces the node touches), else central differences only.
+template <bool FACE>
+__device__ __forceinline__ double split_B_node(const SplitArgs& a, const double* __restrict__ y,
+                                               int N, int n, int i, int j, int k, bool state,
+                                               bool energy) {
+  double g0[3], g1[3], g2[3];
+  if (FACE) {
+    split_gcol(a, y, N, n, 0, i, a.nx, 1, g0);
+    split_gcol(a, y, N, n, 1, j, a.ny, a.nx, g1);
+    split_gcol(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
+  } else {
+    const int sy = a.nx, sz = a.nx * a.ny;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double* v = y + c * N;
+      g0[c] = __ldg(&v[n + 1]) - __ldg(&v[n - 1]);
+      g1[c] = __ldg(&v[n + sy]) - __ldg(&v[n - sy]);
+      g2[c] = __ldg(&v[n + sz]) - __ldg(&v[n - sz]);
+    }
+    g0[0] += a.h2[0];
+    g1[1] += a.h2[1];
+    g2[2] += a.h2[2];
+  }
+  const double det = det3(g0, g1, g2);
+  if (le_zero(det))  // NaN: reported by the error norm
+    atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
+  const double r = 1.0 / det;
+  const double b0 = __ldg(&a.B0s[n]), b1 = __ldg(&a.B0s[N + n]), b2 = __ldg(&a.B0s[2 * N + n]);
+  double B[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    B[c] = (g0[c] * b0 + g1[c] * b1 + g2[c] * b2) * r;
+    a.Bb[c * N + n] = B[c];
+  }
+  a.rb[n] = r;
+  if (!energy) return 0.0;
+  // eq. "magnetic energy": zeta halves per boundary index coordinate
+  const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) + (k == 0 || k == a.nz - 1);
+  const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
+  return zeta * dot3(B, B) * det;
+}
+
+// Pass B (stage s): B and 1/det G at every node, interior nodes (central
+// differences) and boundary nodes (one-sided on their faces) in separate
+// dense loops -- in one loop the compiler evaluates the one-sided variants
+// under predicates for every node, and predicated-off FP64 instructions
+// still take FP64-pipe slots; in the diagnostic launch also the energy
+// partials (eq. "magnetic energy").
 template <int S>
 __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   __shared__ double red[8];
   const int N = a.nx * a.ny * a.nz;
+  const int NI = (a.nx - 2) * (a.ny - 2) * (a.nz - 2);
   const double* y = S == 0 ? a.d[st->cur] : a.ys[S & 1];
+  const bool energy = S == 0 && a.diag;
   double eacc = 0.0;
-  int nb, ne;
-  cta_range(N, nb, ne);
-  for (int n = nb + threadIdx.x; n < ne; n += blockDim.x) {
+  int tb, te;
+  cta_range(NI, tb, te);
+  for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
-    split_nodes(a, n, i, j, k);
-    double g0[3], g1[3], g2[3];
-    split_gcol(a, y, N, n, 0, i, a.nx, 1, g0);
-    split_gcol(a, y, N, n, 1, j, a.ny, a.nx, g1);
-    split_gcol(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
-    const double det = det3(g0, g1, g2);
-    if (le_zero(det))  // NaN: reported by the error norm
-      atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
-    const double r = 1.0 / det;
-    const double b0 = __ldg(&a.B0s[n]), b1 = __ldg(&a.B0s[N + n]), b2 = __ldg(&a.B0s[2 * N + n]);
-    double B[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      B[c] = (g0[c] * b0 + g1[c] * b1 + g2[c] * b2) * r;
-      a.Bb[c * N + n] = B[c];
-    }
-    a.rb[n] = r;
-    if (S == 0 && a.diag) {
-      const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) +
-                     (k == 0 || k == a.nz - 1);
-      const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
-      eacc += zeta * dot3(B, B) * det;
-    }
+    const int n = interior_node(a, t, i, j, k);
+    eacc += split_B_node<false>(a, y, N, n, i, j, k, S == 0, energy);
   }
-  if (S == 0 && a.diag) {
+  cta_range(N - NI, tb, te);
+  for (int b = tb + threadIdx.x; b < te; b += blockDim.x) {
+    int i, j, k;
+    const int n = boundary_node(a, b, i, j, k);
+    eacc += split_B_node<true>(a, y, N, n, i, j, k, S == 0, energy);
+  }
+  if (energy) {
     const int bid = blockIdx.x;
     const double v = block_reduce<false>(eacc, red);
     if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
@@ -141,12 +210,12 @@ __global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
   for (int j = 0; j < 5; ++j) an[j] = (!FINAL && j <= S) ? st->dta[S + 1][j] : 0.0;
   Acc<double> acc;
   const int sy = a.nx, sz = a.nx * a.ny;
-  int nb, ne;
-  cta_range(N, nb, ne);
-  for (int n = nb + threadIdx.x; n < ne; n += blockDim.x) {
+  const int NI = (a.nx - 2) * (a.ny - 2) * (a.nz - 2);
+  int tb, te;
+  cta_range(NI, tb, te);
+  for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
-    split_nodes(a, n, i, j, k);
-    if (i < 1 || i > a.nx - 2 || j < 1 || j > a.ny - 2 || k < 1 || k > a.nz - 2) continue;
+    const int n = interior_node(a, t, i, j, k);
     double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
