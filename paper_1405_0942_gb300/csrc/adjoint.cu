@@ -54,7 +54,11 @@ __device__ __forceinline__ int stencil(int i, int n) {  // 0 central, 1 lower, 2
 }
 
 // Column a of G = index-space differences of y (displacement) + 2 h_a e_a.
-template <typename T>
+// FACE = false: central differences only (the node is interior); kept apart
+// so that the one-sided variants are not evaluated under predicates at
+// interior nodes (predicated-off FP64 instructions still take FP64-pipe
+// slots on GB300).
+template <bool FACE = true, typename T>
 __device__ __forceinline__ void gcol(const AdjGeom& g, const T* y, int N, int a, int i, int j,
                                      int k, double out[3]) {
   const int id[3] = {i, j, k};
@@ -62,11 +66,11 @@ __device__ __forceinline__ void gcol(const AdjGeom& g, const T* y, int N, int a,
   const int st[3] = {1, g.nx, g.nx * g.ny};
   const int c0 = (k * g.ny + j) * g.nx + i;
   const int sa = st[a];
-  const int kind = stencil(id[a], n[a]);
+  const int kind = FACE ? stencil(id[a], n[a]) : 0;
   for (int c = 0; c < 3; ++c) {
     const T* v = y + c * N;
     double d;
-    if (kind == 0)
+    if (!FACE || kind == 0)
       d = (double)v[c0 + sa] - (double)v[c0 - sa];
     else if (kind == 1)
       d = (4.0 * (double)v[c0 + sa] - 3.0 * (double)v[c0]) - (double)v[c0 + 2 * sa];
@@ -89,6 +93,85 @@ __device__ __forceinline__ double dot(const double a[3], const double b[3]) {
 #define NODE_LOOP(N)                                                                      \
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (N); n += gridDim.x * blockDim.x)
 
+// Dense enumerations of node sets, so that a warp's 32 lanes all run the
+// same stencil code: the interior box [1, n-2]^3, the boundary (faces, face
+// by face), and the interior split into the deep box [3, n-4]^3 and the
+// shell between them.
+__device__ __forceinline__ int node_at(const AdjGeom& g, int i, int j, int k) {
+  return (k * g.ny + j) * g.nx + i;
+}
+__device__ __forceinline__ int adj_interior(const AdjGeom& g, int t, int& i, int& j, int& k) {
+  const int nxi = g.nx - 2, nyi = g.ny - 2;
+  i = 1 + t % nxi;
+  const int r = t / nxi;
+  j = 1 + r % nyi;
+  k = 1 + r / nyi;
+  return node_at(g, i, j, k);
+}
+__device__ __forceinline__ int adj_boundary(const AdjGeom& g, int b, int& i, int& j, int& k) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int fz = nx * ny, fy = nx * (nz - 2);
+  if (b < 2 * fz) {
+    k = b < fz ? 0 : nz - 1;
+    const int r = b < fz ? b : b - fz;
+    j = r / nx;
+    i = r - j * nx;
+  } else if (b < 2 * fz + 2 * fy) {
+    int r = b - 2 * fz;
+    j = r < fy ? 0 : ny - 1;
+    r = r < fy ? r : r - fy;
+    k = 1 + r / nx;
+    i = r % nx;
+  } else {
+    const int fx = (ny - 2) * (nz - 2);
+    int r = b - 2 * fz - 2 * fy;
+    i = r < fx ? 0 : nx - 1;
+    r = r < fx ? r : r - fx;
+    k = 1 + r / (ny - 2);
+    j = 1 + r % (ny - 2);
+  }
+  return node_at(g, i, j, k);
+}
+// the deep box exists when every extent is at least 7
+__device__ __forceinline__ bool has_deep(const AdjGeom& g) {
+  return g.nx >= 7 && g.ny >= 7 && g.nz >= 7;
+}
+__device__ __forceinline__ int adj_deep(const AdjGeom& g, int t, int& i, int& j, int& k) {
+  const int dx = g.nx - 6, dy = g.ny - 6;
+  i = 3 + t % dx;
+  const int r = t / dx;
+  j = 3 + r % dy;
+  k = 3 + r / dy;
+  return node_at(g, i, j, k);
+}
+// shell: planes k in {1, 2, nz-3, nz-2} of the interior box, then rows
+// j in {1, 2, ny-3, ny-2} with 3 <= k <= nz-4, then columns i in {1, 2,
+// nx-3, nx-2} with 3 <= j <= ny-4, 3 <= k <= nz-4 (all extents >= 7)
+__device__ __forceinline__ int adj_shell(const AdjGeom& g, int s, int& i, int& j, int& k) {
+  const int ix = g.nx - 2, iy = g.ny - 2, dy = g.ny - 6, dz = g.nz - 6;
+  if (s < 4 * ix * iy) {
+    const int q = s / (ix * iy), r = s - q * ix * iy;
+    k = q < 2 ? 1 + q : g.nz - 5 + q;
+    j = 1 + r / ix;
+    i = 1 + r % ix;
+  } else if (s < 4 * ix * iy + 4 * ix * dz) {
+    const int s1 = s - 4 * ix * iy;
+    const int q = s1 / (ix * dz), r = s1 - q * ix * dz;
+    j = q < 2 ? 1 + q : g.ny - 5 + q;
+    k = 3 + r / ix;
+    i = 1 + r % ix;
+  } else {
+    const int s2 = s - 4 * ix * iy - 4 * ix * dz;
+    const int q = s2 / (dy * dz), r = s2 - q * dy * dz;
+    i = q < 2 ? 1 + q : g.nx - 5 + q;
+    k = 3 + r / dy;
+    j = 3 + r % dy;
+  }
+  return node_at(g, i, j, k);
+}
+#define GRID_LOOP(v, count) \
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (count); v += gridDim.x * blockDim.x)
+
 // y = d + sum_{j<s} dt a_sj k_j (stage input as a displacement), all nodes.
 template <typename T>
 __global__ void k_adj_stage_input(int N3, const T* d, const T* const* k, int s, double dt,
@@ -100,20 +183,34 @@ __global__ void k_adj_stage_input(int N3, const T* d, const T* const* k, int s, 
   }
 }
 
-// B = G B0s / det G and 1/det G at every node of the stage input y.
+// B = G B0s / det G and 1/det G at node n of the stage input y.
+template <bool FACE, typename T>
+__device__ __forceinline__ void fwd_B_node(const AdjGeom& g, const double* y, const T* B0s,
+                                           double* Bb, double* rb, int N, int n, int i, int j,
+                                           int k) {
+  double G[3][3];
+  for (int a = 0; a < 3; ++a) gcol<FACE>(g, y, N, a, i, j, k, G[a]);
+  double m[3];
+  cross3(G[1], G[2], m);
+  const double r = 1.0 / dot(G[0], m);
+  const double b0 = (double)B0s[n], b1 = (double)B0s[N + n], b2 = (double)B0s[2 * N + n];
+  for (int c = 0; c < 3; ++c) Bb[c * N + n] = (G[0][c] * b0 + G[1][c] * b1 + G[2][c] * b2) * r;
+  rb[n] = r;
+}
+
+// B = G B0s / det G and 1/det G at every node (interior, then boundary).
 template <typename T>
 __global__ void k_adj_fwd_B(AdjGeom g, const double* y, const T* B0s, double* Bb, double* rb) {
-  const int N = g.nx * g.ny * g.nz;
-  NODE_LOOP(N) {
-    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
-    double G[3][3];
-    for (int a = 0; a < 3; ++a) gcol(g, y, N, a, i, j, k, G[a]);
-    double m[3];
-    cross3(G[1], G[2], m);
-    const double r = 1.0 / dot(G[0], m);
-    const double b0 = (double)B0s[n], b1 = (double)B0s[N + n], b2 = (double)B0s[2 * N + n];
-    for (int c = 0; c < 3; ++c) Bb[c * N + n] = (G[0][c] * b0 + G[1][c] * b1 + G[2][c] * b2) * r;
-    rb[n] = r;
+  const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+  GRID_LOOP(t, NI) {
+    int i, j, k;
+    const int n = adj_interior(g, t, i, j, k);
+    fwd_B_node<false>(g, y, B0s, Bb, rb, N, n, i, j, k);
+  }
+  GRID_LOOP(b, N - NI) {
+    int i, j, k;
+    const int n = adj_boundary(g, b, i, j, k);
+    fwd_B_node<true>(g, y, B0s, Bb, rb, N, n, i, j, k);
   }
 }
 
@@ -129,7 +226,7 @@ __device__ __forceinline__ void current_at(const AdjGeom& g, const double* y, co
   const int N = g.nx * g.ny * g.nz;
   const int st[3] = {1, g.nx, g.nx * g.ny};
   for (int a = 0; a < 3; ++a) {
-    gcol(g, y, N, a, i, j, k, G[a]);
+    gcol<false>(g, y, N, a, i, j, k, G[a]);  // interior node: central
     for (int c = 0; c < 3; ++c) P[a][c] = Bb[c * N + n + st[a]] - Bb[c * N + n - st[a]];
   }
   cc[0] = dot(P[1], G[2]) - dot(P[2], G[1]);
@@ -149,36 +246,35 @@ __device__ __forceinline__ void current_at(const AdjGeom& g, const double* y, co
 __global__ void k_adj_current(AdjGeom g, const double* y, const double* Bb, const double* rb,
                               const double* lam_u, double* lamP, double* lamg, double* lamr,
                               double* lamB) {
-  const int N = g.nx * g.ny * g.nz;
-  NODE_LOOP(N) {
-    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
+  const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+  GRID_LOOP(t, NI) {
+    int i, j, k;
+    const int n = adj_interior(g, t, i, j, k);
     double lP[3][3] = {{0}}, lg[3][3] = {{0}}, lr = 0.0, lB[3] = {0, 0, 0};
-    if (interior(g, i, j, k)) {
-      double G[3][3], P[3][3], cc[3], V[3], J[3];
-      current_at(g, y, Bb, rb, n, i, j, k, G, P, cc, V, J);
-      const double r = rb[n];
-      const double lu[3] = {lam_u[n], lam_u[N + n], lam_u[2 * N + n]};
-      const double B[3] = {Bb[n], Bb[N + n], Bb[2 * N + n]};
-      double lJ[3];
-      cross3(B, lu, lJ);  // u = J x B: lam_J = B x lam_u, lam_B = lam_u x J
-      cross3(lu, J, lB);
-      double lV[3];
-      for (int c = 0; c < 3; ++c) lV[c] = lJ[c] * r;
-      lr = dot(lJ, V);
-      double lc[3];
-      for (int a = 0; a < 3; ++a) {
-        lc[a] = dot(lV, G[a]);
-        for (int c = 0; c < 3; ++c) lg[a][c] += cc[a] * lV[c];
-      }
-      // c_a = P_{a+1} . g_{a+2} - P_{a+2} . g_{a+1}
-      for (int a = 0; a < 3; ++a) {
-        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-        for (int c = 0; c < 3; ++c) {
-          lP[a1][c] += lc[a] * G[a2][c];
-          lg[a2][c] += lc[a] * P[a1][c];
-          lP[a2][c] -= lc[a] * G[a1][c];
-          lg[a1][c] -= lc[a] * P[a2][c];
-        }
+    double G[3][3], P[3][3], cc[3], V[3], J[3];
+    current_at(g, y, Bb, rb, n, i, j, k, G, P, cc, V, J);
+    const double r = rb[n];
+    const double lu[3] = {lam_u[n], lam_u[N + n], lam_u[2 * N + n]};
+    const double B[3] = {Bb[n], Bb[N + n], Bb[2 * N + n]};
+    double lJ[3];
+    cross3(B, lu, lJ);  // u = J x B: lam_J = B x lam_u, lam_B = lam_u x J
+    cross3(lu, J, lB);
+    double lV[3];
+    for (int c = 0; c < 3; ++c) lV[c] = lJ[c] * r;
+    lr = dot(lJ, V);
+    double lc[3];
+    for (int a = 0; a < 3; ++a) {
+      lc[a] = dot(lV, G[a]);
+      for (int c = 0; c < 3; ++c) lg[a][c] += cc[a] * lV[c];
+    }
+    // c_a = P_{a+1} . g_{a+2} - P_{a+2} . g_{a+1}
+    for (int a = 0; a < 3; ++a) {
+      const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+      for (int c = 0; c < 3; ++c) {
+        lP[a1][c] += lc[a] * G[a2][c];
+        lg[a2][c] += lc[a] * P[a1][c];
+        lP[a2][c] -= lc[a] * G[a1][c];
+        lg[a1][c] -= lc[a] * P[a2][c];
       }
     }
     for (int a = 0; a < 3; ++a)
@@ -189,57 +285,83 @@ __global__ void k_adj_current(AdjGeom g, const double* y, const double* Bb, cons
     lamr[n] = lr;
     for (int c = 0; c < 3; ++c) lamB[c * N + n] = lB[c];
   }
+  GRID_LOOP(b, N - NI) {  // boundary nodes carry no current
+    int i, j, k;
+    const int n = adj_boundary(g, b, i, j, k);
+    for (int q = 0; q < 9; ++q) {
+      lamP[q * N + n] = 0.0;
+      lamg[q * N + n] = 0.0;
+    }
+    lamr[n] = 0.0;
+    for (int c = 0; c < 3; ++c) lamB[c * N + n] = 0.0;
+  }
+}
+
+// The pull-back reverse at node n = (i, j, k).  FACE = false: an interior
+// node (all six neighbours exist, central differences).
+template <bool FACE, typename T>
+__device__ __forceinline__ void pullback_node(const AdjGeom& g, const double* y, const T* B0s,
+                                              const double* rb, const double* lamP, double* lamg,
+                                              const double* lamr, const double* lamB, double wE,
+                                              double* mu, int N, int n, int i, int j, int k) {
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  const int id[3] = {i, j, k};
+  const int ext[3] = {g.nx, g.ny, g.nz};
+  // adjoint of B(n): the centre term plus, since P_a(m) = B(m + e_a) -
+  // B(m - e_a), +lamP_a(n - e_a) and -lamP_a(n + e_a) (zero unless that
+  // neighbour is interior).
+  double lB[3] = {lamB[n], lamB[N + n], lamB[2 * N + n]};
+  for (int a = 0; a < 3; ++a) {
+    if (!FACE || id[a] - 1 >= 0)
+      for (int c = 0; c < 3; ++c) lB[c] += lamP[(a * 3 + c) * N + n - st[a]];
+    if (!FACE || id[a] + 1 < ext[a])
+      for (int c = 0; c < 3; ++c) lB[c] -= lamP[(a * 3 + c) * N + n + st[a]];
+  }
+  double G[3][3];
+  for (int a = 0; a < 3; ++a) gcol<FACE>(g, y, N, a, i, j, k, G[a]);
+  const double r = rb[n];
+  const double b[3] = {(double)B0s[n], (double)B0s[N + n], (double)B0s[2 * N + n]};
+  double W[3];
+  for (int c = 0; c < 3; ++c) W[c] = G[0][c] * b[0] + G[1][c] * b[1] + G[2][c] * b[2];
+  // B = W r
+  double lW[3];
+  for (int c = 0; c < 3; ++c) lW[c] = lB[c] * r;
+  double lr = dot(lB, W) + lamr[n];
+  if (wE != 0.0) {
+    int nb = (i == 0 || i == g.nx - 1) + (j == 0 || j == g.ny - 1) + (k == 0 || k == g.nz - 1);
+    const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
+    for (int c = 0; c < 3; ++c) lW[c] += wE * zeta * W[c] * r / 8.0;
+    lr += wE * zeta * dot(W, W) / 16.0;
+  }
+  // W = sum_a g_a b_a ; r = 1 / det G, d det / d g_a = g_{a+1} x g_{a+2}
+  const double ldet = -lr * r * r;
+  for (int a = 0; a < 3; ++a) {
+    mu[a * N + n] += dot(lW, G[a]);
+    double cr[3];
+    cross3(G[(a + 1) % 3], G[(a + 2) % 3], cr);
+    for (int c = 0; c < 3; ++c) lamg[(a * 3 + c) * N + n] += b[a] * lW[c] + ldet * cr[c];
+  }
 }
 
 // Step 2: gather the adjoint of B, reverse the pull-back, add the energy
 // loss (weight wE; E_M = sum zeta |G B0s|^2 / det G / 16) and the current's
 // g and 1/det adjoints.  lamg is updated in place to the total adjoint of
-// the columns g_a; mu (adjoint of B0s) is accumulated.
+// the columns g_a; mu (adjoint of B0s) is accumulated.  Interior nodes,
+// then boundary nodes.
 template <typename T>
 __global__ void k_adj_pullback(AdjGeom g, const double* y, const T* B0s, const double* rb,
                                const double* lamP, double* lamg, const double* lamr,
                                const double* lamB, double wE, double* mu) {
-  const int N = g.nx * g.ny * g.nz;
-  const int st[3] = {1, g.nx, g.nx * g.ny};
-  NODE_LOOP(N) {
-    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
-    const int id[3] = {i, j, k};
-    const int ext[3] = {g.nx, g.ny, g.nz};
-    // adjoint of B(n): the centre term plus, since P_a(m) = B(m + e_a) -
-    // B(m - e_a), +lamP_a(n - e_a) and -lamP_a(n + e_a) (zero unless that
-    // neighbour is interior).
-    double lB[3] = {lamB[n], lamB[N + n], lamB[2 * N + n]};
-    for (int a = 0; a < 3; ++a) {
-      if (id[a] - 1 >= 0)
-        for (int c = 0; c < 3; ++c) lB[c] += lamP[(a * 3 + c) * N + n - st[a]];
-      if (id[a] + 1 < ext[a])
-        for (int c = 0; c < 3; ++c) lB[c] -= lamP[(a * 3 + c) * N + n + st[a]];
-    }
-    double G[3][3];
-    for (int a = 0; a < 3; ++a) gcol(g, y, N, a, i, j, k, G[a]);
-    const double r = rb[n];
-    const double b[3] = {(double)B0s[n], (double)B0s[N + n], (double)B0s[2 * N + n]};
-    double W[3];
-    for (int c = 0; c < 3; ++c) W[c] = G[0][c] * b[0] + G[1][c] * b[1] + G[2][c] * b[2];
-    // B = W r
-    double lW[3];
-    for (int c = 0; c < 3; ++c) lW[c] = lB[c] * r;
-    double lr = dot(lB, W) + lamr[n];
-    if (wE != 0.0) {
-      int nb = (i == 0 || i == g.nx - 1) + (j == 0 || j == g.ny - 1) + (k == 0 || k == g.nz - 1);
-      const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
-      for (int c = 0; c < 3; ++c) lW[c] += wE * zeta * W[c] * r / 8.0;
-      lr += wE * zeta * dot(W, W) / 16.0;
-    }
-    // W = sum_a g_a b_a ; r = 1 / det G, d det / d g_a = g_{a+1} x g_{a+2}
-    const double ldet = -lr * r * r;
-    for (int a = 0; a < 3; ++a) {
-      mu[a * N + n] += dot(lW, G[a]);
-      double cr[3];
-      cross3(G[(a + 1) % 3], G[(a + 2) % 3], cr);
-      for (int c = 0; c < 3; ++c)
-        lamg[(a * 3 + c) * N + n] += b[a] * lW[c] + ldet * cr[c];
-    }
+  const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+  GRID_LOOP(t, NI) {
+    int i, j, k;
+    const int n = adj_interior(g, t, i, j, k);
+    pullback_node<false>(g, y, B0s, rb, lamP, lamg, lamr, lamB, wE, mu, N, n, i, j, k);
+  }
+  GRID_LOOP(b, N - NI) {
+    int i, j, k;
+    const int n = adj_boundary(g, b, i, j, k);
+    pullback_node<true>(g, y, B0s, rb, lamP, lamg, lamr, lamB, wE, mu, N, n, i, j, k);
   }
 }
 
@@ -252,27 +374,62 @@ __device__ __forceinline__ double gcoef(int m, int p, int n) {
   return p == n - 1 ? 3.0 : (p == n - 2 ? -4.0 : (p == n - 3 ? 1.0 : 0.0));
 }
 
-// Step 3: adjoint of the stage input at interior nodes (0 on the boundary).
-__global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
-  const int N = g.nx * g.ny * g.nz;
+// Adjoint of the stage input at interior node n = (i, j, k), general
+// form: the g_a adjoints of every stencil (central or one-sided) that
+// contains the node.
+__device__ __forceinline__ void positions_general(const AdjGeom& g, const double* lamg,
+                                                  double* lam_y, int N, int n, int i, int j,
+                                                  int k) {
   const int st[3] = {1, g.nx, g.nx * g.ny};
-  NODE_LOOP(N) {
-    const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / (g.nx * g.ny);
-    const int id[3] = {i, j, k};
-    const int ext[3] = {g.nx, g.ny, g.nz};
-    double ly[3] = {0, 0, 0};
-    if (interior(g, i, j, k)) {
-      for (int a = 0; a < 3; ++a)
-        for (int dm = -2; dm <= 2; ++dm) {
-          const int m = id[a] + dm;
-          if (m < 0 || m >= ext[a]) continue;
-          const double w = gcoef(m, id[a], ext[a]);
-          if (w == 0.0) continue;
-          const int nm = n + dm * st[a];
-          for (int c = 0; c < 3; ++c) ly[c] += w * lamg[(a * 3 + c) * N + nm];
-        }
+  const int id[3] = {i, j, k};
+  const int ext[3] = {g.nx, g.ny, g.nz};
+  double ly[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a)
+    for (int dm = -2; dm <= 2; ++dm) {
+      const int m = id[a] + dm;
+      if (m < 0 || m >= ext[a]) continue;
+      const double w = gcoef(m, id[a], ext[a]);
+      if (w == 0.0) continue;
+      const int nm = n + dm * st[a];
+      for (int c = 0; c < 3; ++c) ly[c] += w * lamg[(a * 3 + c) * N + nm];
     }
-    for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+  for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+}
+
+// Step 3: adjoint of the stage input at interior nodes (0 on the boundary).
+// Nodes at least 3 from every face are touched by central stencils only:
+// lam_y = sum_a lamg_a(n - e_a) - lamg_a(n + e_a); the shell between them
+// and the faces takes the general form.
+__global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
+  const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+  const int st[3] = {1, g.nx, g.nx * g.ny};
+  if (has_deep(g)) {
+    const int ND = (g.nx - 6) * (g.ny - 6) * (g.nz - 6);
+    GRID_LOOP(t, ND) {
+      int i, j, k;
+      const int n = adj_deep(g, t, i, j, k);
+      double ly[3] = {0, 0, 0};
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+          ly[c] += lamg[(a * 3 + c) * N + n - st[a]] - lamg[(a * 3 + c) * N + n + st[a]];
+      for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+    }
+    GRID_LOOP(sidx, NI - ND) {
+      int i, j, k;
+      const int n = adj_shell(g, sidx, i, j, k);
+      positions_general(g, lamg, lam_y, N, n, i, j, k);
+    }
+  } else {
+    GRID_LOOP(t, NI) {
+      int i, j, k;
+      const int n = adj_interior(g, t, i, j, k);
+      positions_general(g, lamg, lam_y, N, n, i, j, k);
+    }
+  }
+  GRID_LOOP(b, N - NI) {  // line-tied: no position adjoint
+    int i, j, k;
+    const int n = adj_boundary(g, b, i, j, k);
+    for (int c = 0; c < 3; ++c) lam_y[c * N + n] = 0.0;
   }
 }
 
