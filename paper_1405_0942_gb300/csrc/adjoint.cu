@@ -173,13 +173,30 @@ __device__ __forceinline__ int adj_shell(const AdjGeom& g, int s, int& i, int& j
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (count); v += gridDim.x * blockDim.x)
 
 // y = d + sum_{j<s} dt a_sj k_j (stage input as a displacement), all nodes.
+template <int S, typename T>
+__device__ __forceinline__ void adj_stage_input_s(int N3, const T* d, const T* const* k, double dt,
+                                                  double* y) {
+  double c[S > 0 ? S : 1];
+#pragma unroll
+  for (int j = 0; j < S; ++j) c[j] = dt * AD_A[S][j];
+  NODE_LOOP(N3) {
+    double v = (double)d[n];
+#pragma unroll
+    for (int j = 0; j < S; ++j) v += c[j] * (double)k[j][n];
+    y[n] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_adj_stage_input(int N3, const T* d, const T* const* k, int s, double dt,
                                   double* y) {
-  NODE_LOOP(N3) {
-    double v = (double)d[n];
-    for (int j = 0; j < s; ++j) v += dt * AD_A[s][j] * (double)k[j][n];
-    y[n] = v;
+  switch (s) {  // stage-uniform: the loop over j unrolls without predicates
+    case 0: adj_stage_input_s<0>(N3, d, k, dt, y); break;
+    case 1: adj_stage_input_s<1>(N3, d, k, dt, y); break;
+    case 2: adj_stage_input_s<2>(N3, d, k, dt, y); break;
+    case 3: adj_stage_input_s<3>(N3, d, k, dt, y); break;
+    case 4: adj_stage_input_s<4>(N3, d, k, dt, y); break;
+    default: adj_stage_input_s<5>(N3, d, k, dt, y); break;
   }
 }
 
@@ -435,12 +452,29 @@ __global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
 
 // Reverse Runge-Kutta combine after stage s: lam += lam_y,
 // lam_k_j += dt a_sj lam_y (j < s).
-__global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* lam,
-                         double* const* lam_k) {
+template <int S>
+__device__ __forceinline__ void adj_rk_s(int N3, const double* lam_y, double dt, double* lam,
+                                         double* const* lam_k) {
+  double c[S > 0 ? S : 1];
+#pragma unroll
+  for (int j = 0; j < S; ++j) c[j] = dt * AD_A[S][j];
   NODE_LOOP(N3) {
     const double v = lam_y[n];
     lam[n] += v;
-    for (int j = 0; j < s; ++j) lam_k[j][n] += dt * AD_A[s][j] * v;
+#pragma unroll
+    for (int j = 0; j < S; ++j) lam_k[j][n] += c[j] * v;
+  }
+}
+
+__global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* lam,
+                         double* const* lam_k) {
+  switch (s) {  // stage-uniform: the loop over j unrolls without predicates
+    case 0: adj_rk_s<0>(N3, lam_y, dt, lam, lam_k); break;
+    case 1: adj_rk_s<1>(N3, lam_y, dt, lam, lam_k); break;
+    case 2: adj_rk_s<2>(N3, lam_y, dt, lam, lam_k); break;
+    case 3: adj_rk_s<3>(N3, lam_y, dt, lam, lam_k); break;
+    case 4: adj_rk_s<4>(N3, lam_y, dt, lam, lam_k); break;
+    default: adj_rk_s<5>(N3, lam_y, dt, lam, lam_k); break;
   }
 }
 
