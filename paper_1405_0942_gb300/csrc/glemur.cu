@@ -290,16 +290,20 @@ __device__ __forceinline__ double label(const GridGeom& g, int a, int i) {
 }
 
 template <typename T>
-__global__ void k_set_x(GridGeom g, const double* __restrict__ x, T* d0, T* d1) {
-  const long long N = (long long)g.nx * g.ny * g.nz;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+// d = x - X into both displacement buffers and both stage-input buffers
+// (whose boundary entries must hold the fixed boundary positions).  Grids
+// hold fewer than 2^31 / 3 nodes, so 32-bit indices suffice.
+__global__ void k_set_x(GridGeom g, const double* __restrict__ x, T* d0, T* d1, T* y0, T* y1) {
+  const int N = g.nx * g.ny * g.nz;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    const int i = n % g.nx, r = n / g.nx, j = r % g.ny, k = r / g.ny;
     const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, k)};
     for (int c = 0; c < 3; ++c) {
       const T v = (T)(x[c * N + n] - X[c]);
       d0[c * N + n] = v;
       d1[c * N + n] = v;
+      y0[c * N + n] = v;
+      y1[c * N + n] = v;
     }
   }
 }
@@ -307,11 +311,10 @@ __global__ void k_set_x(GridGeom g, const double* __restrict__ x, T* d0, T* d1) 
 template <typename T>
 __global__ void k_get_x(GridGeom g, const T* const* dbuf, const DevState* st,
                         double* __restrict__ x) {
-  const long long N = (long long)g.nx * g.ny * g.nz;
+  const int N = g.nx * g.ny * g.nz;
   const T* d = dbuf[st->cur];
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % g.nx), j = (int)((n / g.nx) % g.ny), k = (int)(n / ((long long)g.nx * g.ny));
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    const int i = n % g.nx, r = n / g.nx, j = r % g.ny, k = r / g.ny;
     const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, k)};
     for (int c = 0; c < 3; ++c) x[c * N + n] = X[c] + (double)d[c * N + n];
   }
@@ -319,11 +322,10 @@ __global__ void k_get_x(GridGeom g, const T* const* dbuf, const DevState* st,
 
 template <typename T>
 __global__ void k_set_B0(GridGeom g, const double* __restrict__ B0, T* B0s) {
-  const long long N = (long long)g.nx * g.ny * g.nz;
+  const int N = g.nx * g.ny * g.nz;
   // B0s_a = B0_a * 4 h_{a+1} h_{a+2}
   const double s[3] = {4.0 * g.h[1] * g.h[2], 4.0 * g.h[2] * g.h[0], 4.0 * g.h[0] * g.h[1]};
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x)
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
     for (int c = 0; c < 3; ++c) B0s[c * N + n] = (T)(B0[c * N + n] * s[c]);
 }
 
@@ -825,14 +827,15 @@ int glemur_set_x(glemur_ctx* c, const double* x, int mem) {
   if (rc) return rc;
   const int nb = elementwise_blocks(c->N);
   if (c->o.precision == GLEMUR_MIXED)
-    k_set_x<float><<<nb, 256, 0, c->s>>>(geom(c), src, (float*)c->dbuf[0], (float*)c->dbuf[1]);
+    k_set_x<float><<<nb, 256, 0, c->s>>>(geom(c), src, (float*)c->dbuf[0], (float*)c->dbuf[1],
+                                         (float*)c->ys[0], (float*)c->ys[1]);
   else
     k_set_x<double><<<nb, 256, 0, c->s>>>(geom(c), src, (double*)c->dbuf[0],
-                                          (double*)c->dbuf[1]);
+                                          (double*)c->dbuf[1], (double*)c->ys[0],
+                                          (double*)c->ys[1]);
   rc = cuda_rc(cudaGetLastError());
   if (rc) return rc;
-  if ((rc = seed_stage_inputs(c))) return rc;
-  return reset_state(c);
+  return reset_state(c);  // k_set_x also seeded the stage inputs
 }
 
 size_t glemur_state_bytes(const glemur_ctx* c) {
