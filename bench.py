@@ -47,9 +47,9 @@ L2_FLUSH_BYTES = 512 << 20
 # of one attempt's six stages, averaged; FP64: both passes of a stage), keyed
 # by (n, precision, curl); absent workloads report null
 NCU_TRAFFIC = {
-    (64, "fp64", "mimetic"): 45.86e6,
+    (64, "fp64", "mimetic"): 45.88e6,
     (64, "mixed", "mimetic"): 15.71e6,
-    (128, "mixed", "mimetic"): 152.92e6,
+    (128, "mixed", "mimetic"): 152.95e6,
 }
 
 
