@@ -379,6 +379,17 @@ def our_arm(args):
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.sum(axis=1).mean(),
                 "speedup_vs_primary": v2 / value,
                 "roofline": roofline_entry(ms2, w, prec, curl, hbm_peak, peak_kind)}
+        if args.workload == "braid64":
+            # the mixed-precision path where HBM, not L2, holds the fields:
+            # the 128^3 braid of 10 twist regions (mixed-precision workload)
+            w128 = workload("braid128")
+            _, ms3, _ = time_mode(G, torch, w128, "mixed", "mimetic", args.steps, args.warmup,
+                                  flush)
+            v3 = w128.grid.n_interior * 6 * args.steps / (ms3.sum() * 1e-3)
+            extra["mixed_mimetic_braid128"] = {
+                "value": v3, "unit": UNIT, "ms_per_step": ms3.sum(axis=1).mean(),
+                "workload": "braid128", "grid": [128, 128, 128],
+                "roofline": roofline_entry(ms3, w128, "mixed", "mimetic", hbm_peak, peak_kind)}
     e2e = None
     if not args.lean:
         # every rank drives its own replica through the C ABI with host
