@@ -594,6 +594,8 @@ __global__ void k_param_contract(long long M, const double* dB, const double* mu
 namespace glemur {
 // Provided by glemur.cu.
 int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6);
+int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const* yS,
+                               double* const* BS, double* const* RS);
 int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precision,
              void** d_cur, void** B0s, void** k, void** stream);
 }  // namespace glemur
@@ -610,7 +612,7 @@ size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 // xi partials and two small pointer tables.
 struct AdjLayout {
   size_t k6, y, Bb, rb, lamk, lamy, lamP, lamg, lamr, lamB, lamB2, lamu, mu, pv, pi, ptr,
-      total, fstride;
+      yS, BS, RS, total, fstride, rstride;
 };
 
 constexpr int kXiBlocks = 1024;
@@ -637,6 +639,14 @@ AdjLayout adj_layout(int nx, int ny, int nz, int precision) {
   L.pv = o; o += al(kXiBlocks * 8 + 8);
   L.pi = o; o += al(kXiBlocks * 4);
   L.ptr = o; o += 256;
+  // FP64: every stage's input (y_1..y_5), B and 1/det G, kept by the
+  // forward recompute so the reverse loop need not form them again
+  L.rstride = al(N * 8);
+  if (precision == GLEMUR_FP64) {
+    L.yS = o; o += 5 * L.fstride;
+    L.BS = o; o += 6 * L.fstride;
+    L.RS = o; o += 6 * L.rstride;
+  }
   L.total = o;
   return L;
 }
@@ -680,14 +690,32 @@ int nblk(long long n) {
   return (int)(b < 8192 ? (b < 1 ? 1 : b) : 8192);
 }
 
-// The stage VJP at the stage input already in y: lam_u -> lam_y, mu +=.
+// Five stage-input buffers (pointers by value).
+struct YSave {
+  double* p[5];
+};
+
+// Boundary entries of the saved stage inputs y_1..y_5: the fixed boundary
+// positions (the forward passes write interior nodes only).
+__global__ void k_adj_seed_boundary(AdjGeom g, const double* d, YSave ys) {
+  const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
+  GRID_LOOP(b, N - NI) {
+    int i, j, k;
+    const int n = adj_boundary(g, b, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+      const double v = d[c * N + n];
+      for (int q = 0; q < 5; ++q) ys.p[q][c * N + n] = v;
+    }
+  }
+}
+
+// The stage VJP at the stage input y (B and 1/det G in Bb, rb; formed here
+// when form_B): lam_u -> lam_y, mu +=.
 template <typename T>
-void stage_vjp(const Adj& A, const double* lam_u, const double* extra_lamB, double wE) {
+void stage_vjp(const Adj& A, const double* y, double* Bb, double* rb, bool form_B,
+               const double* lam_u, const double* extra_lamB, double wE) {
   const int N = A.N;
-  double* y = A.P(A.L.y);
-  double* Bb = A.P(A.L.Bb);
-  double* rb = A.P(A.L.rb);
-  k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, Bb, rb);
+  if (form_B) k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, Bb, rb);
   if (lam_u) {
     k_adj_current<<<nblk(N), 256, 0, A.s>>>(A.g, y, Bb, rb, lam_u, A.P(A.L.lamP), A.P(A.L.lamg),
                                             A.P(A.L.lamr), A.P(A.L.lamB));
@@ -708,7 +736,25 @@ template <typename T>
 int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, double* lam,
                double* mu_B0) {
   const int N3 = 3 * A.N;
-  int rc = ctx_recompute_stages(c, dt, A.ws + A.L.k6);
+  // FP64 two-pass contexts: the recompute keeps every stage's input, B and
+  // 1/det G; otherwise the reverse loop forms them again
+  double* yS[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* BS[6];
+  double* RS[6];
+  bool saved = false;
+  if (A.precision == GLEMUR_FP64) {
+    YSave ysave;
+    for (int q = 1; q < 6; ++q) ysave.p[q - 1] = yS[q] = A.P(A.L.yS + (q - 1) * A.L.fstride);
+    for (int q = 0; q < 6; ++q) {
+      BS[q] = A.P(A.L.BS + q * A.L.fstride);
+      RS[q] = A.P(A.L.RS + q * A.L.rstride);
+    }
+    k_adj_seed_boundary<<<nblk(A.N), 256, 0, A.s>>>(A.g, (const double*)A.d, ysave);
+    const int rs = ctx_recompute_stages_saved(c, dt, A.ws + A.L.k6, yS, BS, RS);
+    if (rs != GLEMUR_OK && rs != GLEMUR_ERR_BADARG) return rs;
+    saved = rs == GLEMUR_OK;
+  }
+  int rc = saved ? GLEMUR_OK : ctx_recompute_stages(c, dt, A.ws + A.L.k6);
   if (rc) return rc;
   double* lamk_h[6];
   for (int j = 0; j < 6; ++j) lamk_h[j] = A.P(A.L.lamk + j * A.L.fstride);
@@ -722,8 +768,14 @@ int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, d
   k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.mu));
   k_adj_seed<<<nblk(N3), 256, 0, A.s>>>(N3, lam_next, dt, lam, lamk_d);
   for (int s = 5; s >= 0; --s) {
-    k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, s, dt, A.P(A.L.y));
-    stage_vjp<T>(A, lamk_h[s], nullptr, 0.0);
+    if (saved) {
+      stage_vjp<T>(A, s == 0 ? (const double*)A.d : yS[s], BS[s], RS[s], false, lamk_h[s],
+                   nullptr, 0.0);
+    } else {
+      k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, s, dt,
+                                                      A.P(A.L.y));
+      stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, lamk_h[s], nullptr, 0.0);
+    }
     k_adj_rk<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamy), s, dt, lam, lamk_d);
   }
   k_adj_mu_out<<<nblk(A.N), 256, 0, A.s>>>(A.g, A.P(A.L.mu), mu_B0);
@@ -743,7 +795,7 @@ int loss_grad_t(glemur_ctx* c, const Adj& A, int loss, double* value, double* la
   k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, 0, 0.0, A.P(A.L.y));
   double v = 0.0;
   if (loss == 0) {
-    stage_vjp<T>(A, nullptr, nullptr, 1.0);
+    stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, nullptr, nullptr, 1.0);
     int rc = glemur_energy(c, &v);
     if (rc) return rc;
   } else {
@@ -759,7 +811,8 @@ int loss_grad_t(glemur_ctx* c, const Adj& A, int loss, double* value, double* la
     double* out = pv + kXiBlocks;
     k_adj_xi_seed<<<1, 32, 0, A.s>>>(A.g, A.P(A.L.y), Bb, rb, pv, pi, nb, A.P(A.L.lamu),
                                      A.P(A.L.lamB2), out);
-    stage_vjp<T>(A, A.P(A.L.lamu), A.P(A.L.lamB2), 0.0);
+    stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), false, A.P(A.L.lamu), A.P(A.L.lamB2),
+                 0.0);
     if (cudaMemcpyAsync(&v, out, sizeof(double), cudaMemcpyDeviceToHost, A.s))
       return GLEMUR_ERR_CUDA;
   }

@@ -662,6 +662,43 @@ int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6) {
   return cuda_rc(e);
 }
 
+// The same recompute for FP64 two-pass contexts, keeping every stage's
+// data for the adjoint: stage s writes B and 1/det G into BS[s], RS[s]
+// (3N and N doubles) and its next input y_{s+1} into yS[s+1] (3N doubles;
+// the caller has put the boundary positions in yS[1..5]); y_0 is the state
+// itself.  BADARG for other contexts (the caller then recomputes stage data
+// itself).
+int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const* yS,
+                               double* const* BS, double* const* RS) {
+  if (c->o.curl != GLEMUR_CURL_MIMETIC || !c->split) return GLEMUR_ERR_BADARG;
+  k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 0);
+  cudaError_t e = cudaGetLastError();
+  for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
+    SplitArgs a;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    for (int i = 0; i < 3; ++i) a.h2[i] = 2.0 * c->h[i];
+    a.d[0] = (const double*)c->dbuf[0];
+    a.d[1] = (const double*)c->dbuf[1];
+    a.B0s = (const double*)c->B0s;
+    for (int j = 0; j < 5; ++j) a.k[j] = (double*)c->k[j];
+    a.k[5] = s == 5 ? (double*)k6 : nullptr;
+    a.ys[0] = a.ys[1] = nullptr;
+    if (s >= 1) a.ys[s & 1] = yS[s];
+    if (s < 5) a.ys[(s + 1) & 1] = yS[s + 1];
+    a.Bb = BS[s];
+    a.rb = RS[s];
+    a.diag = 0;
+    a.force = 1;
+    a.st = c->st;
+    a.part = c->part;
+    a.nblocks = c->nblocks;
+    e = launch_f64_split(a, s, c->s);
+  }
+  return cuda_rc(e);
+}
+
 // Geometry, storage and the current accepted displacement (synchronises).
 int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precision,
              void** d_cur, void** B0s, void** k, void** stream) {
