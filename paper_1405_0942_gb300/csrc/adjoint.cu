@@ -190,6 +190,8 @@ __device__ __forceinline__ void adj_stage_input_s(int N3, const T* d, const T* c
 template <typename T>
 __global__ void k_adj_stage_input(int N3, const T* d, const T* const* k, int s, double dt,
                                   double* y) {
+  pdl_wait();
+  pdl_trigger();
   switch (s) {  // stage-uniform: the loop over j unrolls without predicates
     case 0: adj_stage_input_s<0>(N3, d, k, dt, y); break;
     case 1: adj_stage_input_s<1>(N3, d, k, dt, y); break;
@@ -218,6 +220,8 @@ __device__ __forceinline__ void fwd_B_node(const AdjGeom& g, const double* y, co
 // B = G B0s / det G and 1/det G at every node (interior, then boundary).
 template <typename T>
 __global__ void k_adj_fwd_B(AdjGeom g, const double* y, const T* B0s, double* Bb, double* rb) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   GRID_LOOP(t, NI) {
     int i, j, k;
@@ -263,6 +267,8 @@ __device__ __forceinline__ void current_at(const AdjGeom& g, const double* y, co
 __global__ void k_adj_current(AdjGeom g, const double* y, const double* Bb, const double* rb,
                               const double* lam_u, double* lamP, double* lamg, double* lamr,
                               double* lamB) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   GRID_LOOP(t, NI) {
     int i, j, k;
@@ -369,6 +375,8 @@ template <typename T>
 __global__ void k_adj_pullback(AdjGeom g, const double* y, const T* B0s, const double* rb,
                                const double* lamP, double* lamg, const double* lamr,
                                const double* lamB, double wE, double* mu) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   GRID_LOOP(t, NI) {
     int i, j, k;
@@ -418,6 +426,8 @@ __device__ __forceinline__ void positions_general(const AdjGeom& g, const double
 // lam_y = sum_a lamg_a(n - e_a) - lamg_a(n + e_a); the shell between them
 // and the faces takes the general form.
 __global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   const int st[3] = {1, g.nx, g.nx * g.ny};
   if (has_deep(g)) {
@@ -468,6 +478,8 @@ __device__ __forceinline__ void adj_rk_s(int N3, const double* lam_y, double dt,
 
 __global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* lam,
                          double* const* lam_k) {
+  pdl_wait();
+  pdl_trigger();
   switch (s) {  // stage-uniform: the loop over j unrolls without predicates
     case 0: adj_rk_s<0>(N3, lam_y, dt, lam, lam_k); break;
     case 1: adj_rk_s<1>(N3, lam_y, dt, lam, lam_k); break;
@@ -481,6 +493,8 @@ __global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* 
 // Seeds of one step's reverse: lam_k_j = dt b_j lam', lam = lam'.
 __global__ void k_adj_seed(int N3, const double* lam_next, double dt, double* lam,
                            double* const* lam_k) {
+  pdl_wait();
+  pdl_trigger();
   NODE_LOOP(N3) {
     const double v = lam_next[n];
     lam[n] = v;
@@ -491,6 +505,8 @@ __global__ void k_adj_seed(int N3, const double* lam_next, double dt, double* la
 // Per-CTA (value, index) of xi = |J x B| / |B|^2 over interior nodes.
 __global__ void k_adj_xi_partial(AdjGeom g, const double* y, const double* Bb, const double* rb,
                                  double* pv, int* pi) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz;
   double best = -1.0;
   int arg = -1;
@@ -534,6 +550,8 @@ __global__ void k_adj_xi_partial(AdjGeom g, const double* y, const double* Bb, c
 __global__ void k_adj_xi_seed(AdjGeom g, const double* y, const double* Bb, const double* rb,
                               const double* pv, const int* pi, int nb, double* lam_u,
                               double* lamB_extra, double* out) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int N = g.nx * g.ny * g.nz;
   double best = -1.0;
@@ -558,15 +576,21 @@ __global__ void k_adj_xi_seed(AdjGeom g, const double* y, const double* Bb, cons
 }
 
 __global__ void k_adj_add(int M, const double* a, double* b) {
+  pdl_wait();
+  pdl_trigger();
   NODE_LOOP(M) b[n] += a[n];
 }
 
 __global__ void k_adj_zero(int M, double* a) {
+  pdl_wait();
+  pdl_trigger();
   NODE_LOOP(M) a[n] = 0.0;
 }
 
 // mu (adjoint of B0s) -> adjoint of B0: B0s_a = s_a B0_a.
 __global__ void k_adj_mu_out(AdjGeom g, const double* mu, double* mu_B0) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz;
   NODE_LOOP(N) for (int c = 0; c < 3; ++c) mu_B0[c * N + n] += g.s[c] * mu[c * N + n];
 }
@@ -574,6 +598,8 @@ __global__ void k_adj_mu_out(AdjGeom g, const double* mu, double* mu_B0) {
 // Parameter contraction out[p] = sum_m dB[p][m] mu[m] (fixed-order sums).
 __global__ void k_param_contract(long long M, const double* dB, const double* mu,
                                  double* out) {
+  pdl_wait();
+  pdl_trigger();
   const int p = blockIdx.x;
   double s = 0.0;
   for (long long m = threadIdx.x; m < M; m += blockDim.x) s += dB[p * M + m] * mu[m];
@@ -698,6 +724,8 @@ struct YSave {
 // Boundary entries of the saved stage inputs y_1..y_5: the fixed boundary
 // positions (the forward passes write interior nodes only).
 __global__ void k_adj_seed_boundary(AdjGeom g, const double* d, YSave ys) {
+  pdl_wait();
+  pdl_trigger();
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   GRID_LOOP(b, N - NI) {
     int i, j, k;
@@ -715,21 +743,22 @@ template <typename T>
 void stage_vjp(const Adj& A, const double* y, double* Bb, double* rb, bool form_B,
                const double* lam_u, const double* extra_lamB, double wE) {
   const int N = A.N;
-  if (form_B) k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, Bb, rb);
+  if (form_B) launch_pdl(k_adj_fwd_B<T>, dim3(nblk(N)), dim3(256), 0, A.s, A.g, y, (const T*)A.B0s,
+                         Bb, rb);
   if (lam_u) {
-    k_adj_current<<<nblk(N), 256, 0, A.s>>>(A.g, y, Bb, rb, lam_u, A.P(A.L.lamP), A.P(A.L.lamg),
-                                            A.P(A.L.lamr), A.P(A.L.lamB));
+    launch_pdl(k_adj_current, dim3(nblk(N)), dim3(256), 0, A.s, A.g, y, Bb, rb, lam_u,
+               A.P(A.L.lamP), A.P(A.L.lamg), A.P(A.L.lamr), A.P(A.L.lamB));
   } else {
-    k_adj_zero<<<nblk(9 * N), 256, 0, A.s>>>(9 * N, A.P(A.L.lamP));
-    k_adj_zero<<<nblk(9 * N), 256, 0, A.s>>>(9 * N, A.P(A.L.lamg));
-    k_adj_zero<<<nblk(N), 256, 0, A.s>>>(N, A.P(A.L.lamr));
-    k_adj_zero<<<nblk(3 * N), 256, 0, A.s>>>(3 * N, A.P(A.L.lamB));
+    launch_pdl(k_adj_zero, dim3(nblk(9 * N)), dim3(256), 0, A.s, 9 * N, A.P(A.L.lamP));
+    launch_pdl(k_adj_zero, dim3(nblk(9 * N)), dim3(256), 0, A.s, 9 * N, A.P(A.L.lamg));
+    launch_pdl(k_adj_zero, dim3(nblk(N)), dim3(256), 0, A.s, N, A.P(A.L.lamr));
+    launch_pdl(k_adj_zero, dim3(nblk(3 * N)), dim3(256), 0, A.s, 3 * N, A.P(A.L.lamB));
   }
-  if (extra_lamB) k_adj_add<<<nblk(3 * N), 256, 0, A.s>>>(3 * N, extra_lamB, A.P(A.L.lamB));
-  k_adj_pullback<T><<<nblk(N), 256, 0, A.s>>>(A.g, y, (const T*)A.B0s, rb, A.P(A.L.lamP),
-                                               A.P(A.L.lamg), A.P(A.L.lamr), A.P(A.L.lamB), wE,
-                                               A.P(A.L.mu));
-  k_adj_positions<<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.lamg), A.P(A.L.lamy));
+  if (extra_lamB) launch_pdl(k_adj_add, dim3(nblk(3 * N)), dim3(256), 0, A.s, 3 * N, extra_lamB,
+                             A.P(A.L.lamB));
+  launch_pdl(k_adj_pullback<T>, dim3(nblk(N)), dim3(256), 0, A.s, A.g, y, (const T*)A.B0s, rb,
+             A.P(A.L.lamP), A.P(A.L.lamg), A.P(A.L.lamr), A.P(A.L.lamB), wE, A.P(A.L.mu));
+  launch_pdl(k_adj_positions, dim3(nblk(N)), dim3(256), 0, A.s, A.g, A.P(A.L.lamg), A.P(A.L.lamy));
 }
 
 template <typename T>
@@ -749,7 +778,8 @@ int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, d
       BS[q] = A.P(A.L.BS + q * A.L.fstride);
       RS[q] = A.P(A.L.RS + q * A.L.rstride);
     }
-    k_adj_seed_boundary<<<nblk(A.N), 256, 0, A.s>>>(A.g, (const double*)A.d, ysave);
+    launch_pdl(k_adj_seed_boundary, dim3(nblk(A.N)), dim3(256), 0, A.s, A.g, (const double*)A.d,
+               ysave);
     const int rs = ctx_recompute_stages_saved(c, dt, A.ws + A.L.k6, yS, BS, RS);
     if (rs != GLEMUR_OK && rs != GLEMUR_ERR_BADARG) return rs;
     saved = rs == GLEMUR_OK;
@@ -765,20 +795,20 @@ int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, d
   cudaError_t e = cudaMemcpyAsync(lamk_d, lamk_h, sizeof(lamk_h), cudaMemcpyHostToDevice, A.s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(kp_d, kp, sizeof(kp), cudaMemcpyHostToDevice, A.s);
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
-  k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.mu));
-  k_adj_seed<<<nblk(N3), 256, 0, A.s>>>(N3, lam_next, dt, lam, lamk_d);
+  launch_pdl(k_adj_zero, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.mu));
+  launch_pdl(k_adj_seed, dim3(nblk(N3)), dim3(256), 0, A.s, N3, lam_next, dt, lam, lamk_d);
   for (int s = 5; s >= 0; --s) {
     if (saved) {
       stage_vjp<T>(A, s == 0 ? (const double*)A.d : yS[s], BS[s], RS[s], false, lamk_h[s],
                    nullptr, 0.0);
     } else {
-      k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, s, dt,
-                                                      A.P(A.L.y));
+      launch_pdl(k_adj_stage_input<T>, dim3(nblk(N3)), dim3(256), 0, A.s, N3, (const T*)A.d, kp_d,
+                 s, dt, A.P(A.L.y));
       stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, lamk_h[s], nullptr, 0.0);
     }
-    k_adj_rk<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamy), s, dt, lam, lamk_d);
+    launch_pdl(k_adj_rk, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.lamy), s, dt, lam, lamk_d);
   }
-  k_adj_mu_out<<<nblk(A.N), 256, 0, A.s>>>(A.g, A.P(A.L.mu), mu_B0);
+  launch_pdl(k_adj_mu_out, dim3(nblk(A.N)), dim3(256), 0, A.s, A.g, A.P(A.L.mu), mu_B0);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(A.s);  // pointer tables are host stack
   return e == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA;
@@ -791,8 +821,9 @@ int loss_grad_t(glemur_ctx* c, const Adj& A, int loss, double* value, double* la
   const T* kp[1] = {nullptr};
   const T** kp_d = (const T**)(A.ws + A.L.ptr + 64);
   if (cudaMemcpyAsync(kp_d, kp, sizeof(kp), cudaMemcpyHostToDevice, A.s)) return GLEMUR_ERR_CUDA;
-  k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.mu));
-  k_adj_stage_input<T><<<nblk(N3), 256, 0, A.s>>>(N3, (const T*)A.d, kp_d, 0, 0.0, A.P(A.L.y));
+  launch_pdl(k_adj_zero, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.mu));
+  launch_pdl(k_adj_stage_input<T>, dim3(nblk(N3)), dim3(256), 0, A.s, N3, (const T*)A.d, kp_d, 0,
+             0.0, A.P(A.L.y));
   double v = 0.0;
   if (loss == 0) {
     stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, nullptr, nullptr, 1.0);
@@ -801,23 +832,24 @@ int loss_grad_t(glemur_ctx* c, const Adj& A, int loss, double* value, double* la
   } else {
     double* Bb = A.P(A.L.Bb);
     double* rb = A.P(A.L.rb);
-    k_adj_fwd_B<T><<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.y), (const T*)A.B0s, Bb, rb);
+    launch_pdl(k_adj_fwd_B<T>, dim3(nblk(N)), dim3(256), 0, A.s, A.g, A.P(A.L.y), (const T*)A.B0s,
+               Bb, rb);
     const int nb = nblk(N) < kXiBlocks ? nblk(N) : kXiBlocks;
     double* pv = A.P(A.L.pv);
     int* pi = (int*)(A.ws + A.L.pi);
-    k_adj_xi_partial<<<nb, 256, 0, A.s>>>(A.g, A.P(A.L.y), Bb, rb, pv, pi);
-    k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamu));
-    k_adj_zero<<<nblk(N3), 256, 0, A.s>>>(N3, A.P(A.L.lamB2));
+    launch_pdl(k_adj_xi_partial, dim3(nb), dim3(256), 0, A.s, A.g, A.P(A.L.y), Bb, rb, pv, pi);
+    launch_pdl(k_adj_zero, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.lamu));
+    launch_pdl(k_adj_zero, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.lamB2));
     double* out = pv + kXiBlocks;
-    k_adj_xi_seed<<<1, 32, 0, A.s>>>(A.g, A.P(A.L.y), Bb, rb, pv, pi, nb, A.P(A.L.lamu),
-                                     A.P(A.L.lamB2), out);
+    launch_pdl(k_adj_xi_seed, dim3(1), dim3(32), 0, A.s, A.g, A.P(A.L.y), Bb, rb, pv, pi, nb,
+               A.P(A.L.lamu), A.P(A.L.lamB2), out);
     stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), false, A.P(A.L.lamu), A.P(A.L.lamB2),
                  0.0);
     if (cudaMemcpyAsync(&v, out, sizeof(double), cudaMemcpyDeviceToHost, A.s))
       return GLEMUR_ERR_CUDA;
   }
   cudaMemcpyAsync(lam, A.P(A.L.lamy), sizeof(double) * N3, cudaMemcpyDeviceToDevice, A.s);
-  k_adj_mu_out<<<nblk(N), 256, 0, A.s>>>(A.g, A.P(A.L.mu), mu_B0);
+  launch_pdl(k_adj_mu_out, dim3(nblk(N)), dim3(256), 0, A.s, A.g, A.P(A.L.mu), mu_B0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(A.s);
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
@@ -859,7 +891,7 @@ int glemur_loss_grad(glemur_ctx* c, int loss, double* value, double* lam, double
 int glemur_param_contract(int n_params, long long m, const double* dB0, const double* mu,
                           double* out, void* stream) {
   if (n_params < 1 || m < 1 || !dB0 || !mu || !out) return GLEMUR_ERR_BADARG;
-  k_param_contract<<<n_params, 256, 0, (cudaStream_t)stream>>>(m, dB0, mu, out);
+  launch_pdl(k_param_contract, dim3(n_params), dim3(256), 0, (cudaStream_t)stream, m, dB0, mu, out);
   return cudaGetLastError() == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA;
 }
 

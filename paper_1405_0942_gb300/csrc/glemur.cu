@@ -192,7 +192,17 @@ __device__ void set_coeffs_parallel(DevState* st, double dt) {
 // Thread 0 takes the decision from a snapshot of the control state (all
 // loads independent, then all stores); the block then writes the dt-scaled
 // coefficients of the next attempt in parallel.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("GLEMUR_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
+  pdl_trigger();
+  pdl_wait();
   if (st->status != ST_OK || st->n_accept >= st->target) return;
   __shared__ double sh[96];
   __shared__ double dt_next;
@@ -533,8 +543,8 @@ cudaError_t launch_attempt(const glemur_ctx* c) {
     cudaError_t e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
     if (e != cudaSuccess) return e;
   }
-  k_control<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, c->o.curl), diag);
-  return cudaGetLastError();
+  return launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
+                    nblocks_of(c, c->o.curl), diag);
 }
 
 int read_state(glemur_ctx* c, DevState* hs) {
@@ -1054,8 +1064,8 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
   if (e == cudaSuccess) {
-    k_control<<<1, 256, 0, c->s>>>(c->st, c->part, nblocks_of(c, c->o.curl), diag);
-    e = cudaGetLastError();
+    e = launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
+                   nblocks_of(c, c->o.curl), diag);
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->s);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);

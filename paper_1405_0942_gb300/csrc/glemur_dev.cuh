@@ -108,6 +108,42 @@ struct StageArgs {
   unsigned tma_test_extra;
 };
 
+// Programmatic dependent launch.  The kernels of an attempt are launched
+// with launch_pdl: the next kernel of the stream may then be scheduled onto
+// SMs that the current one has left while its last CTAs still run.  Each
+// such kernel calls pdl_trigger() (its own successor may be scheduled once
+// all of its CTAs have started) and pdl_wait() before it reads or writes
+// anything an earlier kernel of the stream touches, DevState included:
+// griddepcontrol.wait returns once the preceding grids have completed and
+// their memory operations are visible.  Every path through such a kernel
+// passes pdl_wait(), so completion stays transitive along the stream.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Host side: launch `k` on stream s, programmatic serialisation allowed
+// unless the environment sets GLEMUR_PDL=0 (then an ordinary launch).  A
+// grid launched this way is placed on SMs as slots free up, not spread
+// evenly at launch: the one-wave FP64 passes therefore size their grid to
+// exactly the CTAs per SM that each of them can hold.
+bool pdl_enabled();
+template <typename... Exp, typename... Act>
+cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Act&&>(args)...);
+}
+
 __device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {
   return ((long long)k * ny + j) * nx + i;
 }

@@ -19,7 +19,9 @@
 // Both run one wave of CTAs (as many as fit on the SMs), each over a
 // contiguous range of whole warps of nodes: the FP64 pipe is per SM, so
 // every SM gets the same number of node-warps (to within one per CTA) and
-// no SM idles while another finishes a second round.  The per-CTA partials
+// no SM idles while another finishes a second round.  Each pass is launched
+// as a programmatic dependent of the one before it (launch_pdl), so its
+// CTAs take the SMs the previous pass leaves and start as soon as it ends.  The per-CTA partials
 // (Lambda, E_M, xi) keep the fused kernel's layout.
 #include "stage_kernels.cuh"
 
@@ -163,6 +165,7 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
 // partials (eq. "magnetic energy").
 template <int S>
 __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
+  pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   __shared__ double red[8];
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
     const int n = boundary_node(a, b, i, j, k);
     eacc += split_B_node<true>(a, y, N, n, i, j, k, S == 0, energy);
   }
+  pdl_trigger();
   if (energy) {
     const int bid = blockIdx.x;
     const double v = block_reduce<false>(eacc, red);
@@ -192,10 +196,14 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
 }
 
 // Pass C (stage s): current and velocity at interior nodes; k_s and the
-// next stage input, or (s = 5) the update, the error and k6.
+// next stage input, or (s = 5) the update, the error and k6.  Held to 64
+// registers (a few spilled values in two of the stages) so that an SM holds
+// four CTAs of either pass: the grid is then exactly four per SM, and a
+// launch that starts while the previous pass drains cannot crowd one SM.
 template <int S>
-__global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
+__global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
   constexpr bool FINAL = S == 5;
+  pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   __shared__ double red[8];
@@ -282,6 +290,7 @@ __global__ void __launch_bounds__(256) k_split_C(const SplitArgs a) {
       }
     }
   }
+  pdl_trigger();
   const int bid = blockIdx.x;
   if (FINAL) {
     const double v = block_reduce<true>(acc.lam, red);
@@ -307,10 +316,11 @@ int split_ctas_per_sm() {
 // Launch both passes of stage s on `nblocks` CTAs of 256 threads.
 cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s) {
   const dim3 g(a.nblocks);
-#define GLEMUR_SPLIT_CASE(SS)                        \
-  case SS:                                           \
-    k_split_B<SS><<<g, 256, 0, s>>>(a);              \
-    k_split_C<SS><<<g, 256, 0, s>>>(a);              \
+  cudaError_t e = cudaSuccess;
+#define GLEMUR_SPLIT_CASE(SS)                                   \
+  case SS:                                                      \
+    e = launch_pdl(k_split_B<SS>, g, dim3(256), 0, s, a);       \
+    if (e == cudaSuccess) e = launch_pdl(k_split_C<SS>, g, dim3(256), 0, s, a); \
     break;
   switch (stage) {
     GLEMUR_SPLIT_CASE(0)
@@ -323,7 +333,7 @@ cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s) {
       return cudaErrorInvalidValue;
   }
 #undef GLEMUR_SPLIT_CASE
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace glemur

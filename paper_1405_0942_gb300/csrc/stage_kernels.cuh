@@ -563,6 +563,7 @@ __device__ __forceinline__ void write_partials(const StageArgs<T>& a, bool final
 template <typename T, typename C, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a) {
   constexpr bool FINAL = S == 5;
+  pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -624,6 +625,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_mimetic(const StageArgs<T> a
     if (load) yp.commit(pts.off, xs + xslot(qn) * XP);
     __syncthreads();
   }
+  pdl_trigger();
   write_partials<T, C>(a, FINAL, diag, acc, red);
 }
 
@@ -736,6 +738,7 @@ __device__ __forceinline__ void direct_out(const StageArgs<T>& a, int n,
 template <typename T, typename C, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a) {
   constexpr bool FINAL = S == 5;
+  pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -782,6 +785,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage_direct(const StageArgs<T> a)
     if (load) raw.template commit<DP>(pts.off, xs + (ql & 3) * 3 * DP);
     __syncthreads();
   }
+  pdl_trigger();
   write_partials<T, C>(a, FINAL, diag, acc, red);
 }
 
@@ -796,13 +800,12 @@ inline size_t stage_smem_bytes(int curl, size_t csize) {
 template <typename T, typename C, int CURL, int MINB>
 cudaError_t launch_stage_t(const StageArgs<T>& a, int stage, dim3 grid, cudaStream_t s) {
   const size_t smem = stage_smem_bytes(CURL, sizeof(C));
-#define GLEMUR_STAGE_CASE(SS)                                              \
-  case SS:                                                                 \
-    if constexpr (CURL == 0)                                               \
-      k_stage_mimetic<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);           \
-    else                                                                   \
-      k_stage_direct<T, C, SS, MINB><<<grid, NT, smem, s>>>(a);            \
-    break;
+#define GLEMUR_STAGE_CASE(SS)                                                     \
+  case SS:                                                                        \
+    if constexpr (CURL == 0)                                                      \
+      return launch_pdl(k_stage_mimetic<T, C, SS, MINB>, grid, dim3(NT), smem, s, a); \
+    else                                                                          \
+      return launch_pdl(k_stage_direct<T, C, SS, MINB>, grid, dim3(NT), smem, s, a);
   switch (stage) {
     GLEMUR_STAGE_CASE(0)
     GLEMUR_STAGE_CASE(1)
@@ -814,7 +817,6 @@ cudaError_t launch_stage_t(const StageArgs<T>& a, int stage, dim3 grid, cudaStre
       return cudaErrorInvalidValue;
   }
 #undef GLEMUR_STAGE_CASE
-  return cudaGetLastError();
 }
 
 template <typename T, typename C, int CURL, int MINB>

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
   using Gm = TmaGeo<WARPS, R>;
   constexpr bool FINAL = S == 5;
+  pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   if (st->flags & FLAG_TIMEOUT) return;  // an earlier stage of this attempt gave up
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     bs0 = (bs0 + 1) & (BRING - 1);
     __syncthreads();
   }
+  pdl_trigger();
   if (__syncthreads_or(acc.bad) && threadIdx.x == 0)
     atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   write_partials<float, float>(a, FINAL, diag, acc, red);
@@ -370,15 +372,14 @@ cudaError_t launch_stage_tma_t(const StageArgs<float>& a, const TmaMaps& maps, i
   const size_t smem = Gm::smem_bytes();
   const int nt = Gm::NTH;
   switch (stage) {
-    case 0: k_stage_mimetic_tma<WARPS, R, 0, MINB><<<grid, nt, smem, s>>>(a, maps); break;
-    case 1: k_stage_mimetic_tma<WARPS, R, 1, MINB><<<grid, nt, smem, s>>>(a, maps); break;
-    case 2: k_stage_mimetic_tma<WARPS, R, 2, MINB><<<grid, nt, smem, s>>>(a, maps); break;
-    case 3: k_stage_mimetic_tma<WARPS, R, 3, MINB><<<grid, nt, smem, s>>>(a, maps); break;
-    case 4: k_stage_mimetic_tma<WARPS, R, 4, MINB><<<grid, nt, smem, s>>>(a, maps); break;
-    case 5: k_stage_mimetic_tma<WARPS, R, 5, MINB><<<grid, nt, smem, s>>>(a, maps); break;
+    case 0: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 0, MINB>, grid, dim3(nt), smem, s, a, maps);
+    case 1: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 1, MINB>, grid, dim3(nt), smem, s, a, maps);
+    case 2: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 2, MINB>, grid, dim3(nt), smem, s, a, maps);
+    case 3: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 3, MINB>, grid, dim3(nt), smem, s, a, maps);
+    case 4: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 4, MINB>, grid, dim3(nt), smem, s, a, maps);
+    case 5: return launch_pdl(k_stage_mimetic_tma<WARPS, R, 5, MINB>, grid, dim3(nt), smem, s, a, maps);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int WARPS, int R, int MINB>
