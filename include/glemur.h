@@ -138,7 +138,13 @@ size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
  *                         the cost model's choice
  *   GLEMUR_TEST_TMA_TIMEOUT=1  test hook: every TMA tile wait expects 16
  *                         bytes that never arrive, so the bounded wait gives
- *                         up and steps fail with GLEMUR_ERR_TIMEOUT */
+ *                         up and steps fail with GLEMUR_ERR_TIMEOUT
+ * and, read once per process, for every launch of the library:
+ *   GLEMUR_PDL=0          ordinary kernel launches instead of programmatic
+ *                         dependent launches (each kernel of an attempt or
+ *                         reverse step may otherwise be scheduled while the
+ *                         previous one drains; it waits for that kernel's
+ *                         completion before it touches memory) */
 int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz,
                      const double lo[3], const double hi[3],
                      const glemur_opts* opts, void* stream, void* workspace,

@@ -102,10 +102,25 @@ __device__ __forceinline__ C dot3(const C a[3], const C b[3]) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// 1/det: IEEE division in FP64; in mixed precision the determinant is
-// already carried beyond FP32 and the reciprocal only scales FP32 data, so
-// the fast reciprocal (about 2 ulp) is used.
-__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+// 1/det.  FP64: Newton-Raphson refinement of the hardware approximation
+// rcp.approx.ftz.f64, y <- y + y (1 - v y): each step squares the relative
+// error (the classical iteration for reciprocals, e.g. Muller et al.,
+// Handbook of Floating-Point Arithmetic, ch. on Newton-Raphson division),
+// so two steps take the approximation to within an ulp or two of the
+// correctly rounded 1/v in 4 FMAs, where the IEEE division costs about 12
+// FP64-pipe instructions -- a quarter of the FP64 work of forming B.  NaN
+// propagates; 0 and subnormal v give NaN or inf, and every caller has
+// already flagged det <= 0.  In mixed precision the determinant is already
+// carried beyond FP32 and the reciprocal only scales FP32 data, so the fast
+// FP32 reciprocal (about 2 ulp) is used.
+__device__ __forceinline__ double recip(double v) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(v));
+  double e = fma(-v, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-v, y, 1.0);
+  return fma(y, e, y);
+}
 __device__ __forceinline__ float recip(float v) { return __fdividef(1.0f, v); }
 
 __device__ __forceinline__ float nanmaxf_(float a, float b) {
