@@ -300,22 +300,22 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
       tma_compute_B<Gm>(a, q, k0, k1, bp, nullptr, b0v, Rg, bs + bslot(q) * Gm::BPt, diag, acc);
     }
   __syncthreads();
-  // ring slots of plane m (y_s: 6, B: 4), advanced without divisions
-  int ys0 = xslot(k0), bs0 = bslot(k0);
+  // ring slot offsets of the y_s planes m-1 .. m+4 and the B planes
+  // m-1 .. m+2; one plane on, each list rotates by one (the slot of plane
+  // m-1 is the slot of plane m+5, resp. m+3)
+  int yo[6], bo[4];
+#pragma unroll
+  for (int dd = 0; dd < 6; ++dd) yo[dd] = xslot(k0 + dd - 1) * Gm::YSTRt;
+#pragma unroll
+  for (int dd = 0; dd < 4; ++dd) bo[dd] = bslot(k0 + dd - 1) * Gm::BPt;
   for (int m = k0; m < k1; ++m) {
     const int it = m - k0;
-    // y_s planes m-1 .. m+4 and B planes m-1 .. m+2
     const float* yl[6];
 #pragma unroll
-    for (int dd = 0; dd < 6; ++dd) {
-      int sl = ys0 + dd - 1;
-      sl += sl < 0 ? XRING : 0;
-      sl -= sl >= XRING ? XRING : 0;
-      yl[dd] = yr + sl * Gm::YSTRt;
-    }
+    for (int dd = 0; dd < 6; ++dd) yl[dd] = yr + yo[dd];
     V4<float>* bl[4];
 #pragma unroll
-    for (int dd = 0; dd < 4; ++dd) bl[dd] = bs + ((bs0 + dd + BRING - 1) & (BRING - 1)) * Gm::BPt;
+    for (int dd = 0; dd < 4; ++dd) bl[dd] = bs + bo[dd];
     if (threadIdx.x == 0) {
       const bool ly = m + 4 < a.nz && m + 4 <= k1 + 1;
       const bool lz = m + 3 < a.nz && m + 3 <= k1;
@@ -354,8 +354,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         tma_mimetic_out<Gm, S>(a, ty + r * WARPS, m * nxy + nxy_out + r * WARPS * a.nx, yl[0],
                                yl[1], yl[2], bl[0], bl[1], bl[2], ce[r], dout, an, st, diag,
                                acc);
-    ys0 = ys0 == XRING - 1 ? 0 : ys0 + 1;
-    bs0 = (bs0 + 1) & (BRING - 1);
+    const int y_first = yo[0], b_first = bo[0];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) yo[dd] = yo[dd + 1];
+    yo[5] = y_first;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) bo[dd] = bo[dd + 1];
+    bo[3] = b_first;
     __syncthreads();
   }
   pdl_trigger();
