@@ -34,22 +34,8 @@ cudaError_t prepare_f32_mimetic_tma();
 int ctas_per_sm_f32_mimetic_tma();
 int tile_rows_f32_mimetic_tma();
 
-struct SplitArgs {
-  int nx, ny, nz;
-  double h2[3];
-  const double* d[2];
-  const double* B0s;
-  double* k[6];
-  double* ys[2];
-  double* Bb;
-  double* rb;
-  int diag, force;
-  DevState* st;
-  double* part;
-  int nblocks;
-};
 cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s);
-int split_ctas_per_sm();
+void split_ctas_per_sm(int b[6], int c[6]);
 
 // Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
 // of section "Time Stepping".
@@ -374,6 +360,7 @@ struct glemur_ctx {
   double* Bb;                            // split path: B
   double* rb;                            // split path: 1/det G
   int max_blocks, nblocks, kz;          // mimetic-current launches
+  int split_grid_b[6] = {}, split_grid_c[6] = {};  // FP64 two-pass grids (CTAs)
   int nblocks_direct, kz_direct;         // direct-current launches
   dim3 grid, grid_direct;
   int nsm;
@@ -509,6 +496,10 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
+  for (int j = 0; j < 6; ++j) {
+    a.grid_b[j] = c->split_grid_b[j];
+    a.grid_c[j] = c->split_grid_c[j];
+  }
   return launch_f64_split(a, stage, c->s);
 }
 
@@ -704,6 +695,10 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
     a.st = c->st;
     a.part = c->part;
     a.nblocks = c->nblocks;
+    for (int j = 0; j < 6; ++j) {
+      a.grid_b[j] = c->split_grid_b[j];
+      a.grid_c[j] = c->split_grid_c[j];
+    }
     e = launch_f64_split(a, s, c->s);
   }
   return cuda_rc(e);
@@ -842,10 +837,19 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->grid = dim3(gx, gym, (nz + c->kz - 1) / c->kz);
   c->nblocks = gx * gym * (int)c->grid.z;
   if (c->split) {
-    // one wave of CTAs of 256 threads, each over an equal range of node warps
+    // per pass one wave of CTAs of 256 threads, each over an equal range of
+    // node warps; the partials' stride is the larger grid
+    int ob[6], oc[6];
+    split_ctas_per_sm(ob, oc);
     const long long need = (c->N + 255) / 256;
-    const long long cap = (long long)split_ctas_per_sm() * c->nsm;
-    c->nblocks = (int)(need < cap ? need : cap);
+    c->nblocks = 1;
+    for (int s = 0; s < 6; ++s) {
+      const long long cb = (long long)ob[s] * c->nsm, cc = (long long)oc[s] * c->nsm;
+      c->split_grid_b[s] = (int)(need < cb ? need : cb);
+      c->split_grid_c[s] = (int)(need < cc ? need : cc);
+      c->nblocks = c->split_grid_b[s] > c->nblocks ? c->split_grid_b[s] : c->nblocks;
+      c->nblocks = c->split_grid_c[s] > c->nblocks ? c->split_grid_c[s] : c->nblocks;
+    }
   }
   c->kz_direct = choose_kz(nz, gx * gy, c->nsm, pd, !mixed);
   c->grid_direct = dim3(gx, gy, (nz + c->kz_direct - 1) / c->kz_direct);

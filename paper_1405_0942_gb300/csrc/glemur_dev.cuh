@@ -144,6 +144,26 @@ cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cu
   return cudaLaunchKernelEx(&cfg, k, static_cast<Act&&>(args)...);
 }
 
+// Arguments of the FP64 two-pass stages (pass B: B and 1/det G at every
+// node; pass C: current, k_s and the next stage input).
+struct SplitArgs {
+  int nx, ny, nz;
+  double h2[3];        // 2 h_a
+  const double* d[2];  // ping-pong displacements
+  const double* B0s;   // pre-scaled B0 (3N)
+  double* k[6];        // k1..k5 (k[5] = optional k6)
+  double* ys[2];       // stage inputs: y_s in ys[s & 1] (s >= 1), 3N each;
+                       // boundary entries hold the fixed boundary positions
+  double* Bb;          // B, 3N
+  double* rb;          // 1/det G, N
+  int diag, force;
+  DevState* st;
+  double* part;        // [NPART][nblocks] per-CTA partials
+  int nblocks;         // partial stride: the largest of the grids
+  int grid_b[6];       // CTAs of pass B of each stage
+  int grid_c[6];       // CTAs of pass C of each stage
+};
+
 __device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {
   return ((long long)k * ny + j) * nx + i;
 }

@@ -16,32 +16,18 @@
 //            k_s and, pointwise, the next stage input
 //            y_{s+1} = d + sum_{j<=s} dt a_{s+1,j} k_j; the last stage
 //            writes the fifth-order update and the embedded error instead.
-// Both run one wave of CTAs (as many as fit on the SMs), each over a
-// contiguous range of whole warps of nodes: the FP64 pipe is per SM, so
-// every SM gets the same number of node-warps (to within one per CTA) and
-// no SM idles while another finishes a second round.  Each pass is launched
-// as a programmatic dependent of the one before it (launch_pdl), so its
-// CTAs take the SMs the previous pass leaves and start as soon as it ends.  The per-CTA partials
-// (Lambda, E_M, xi) keep the fused kernel's layout.
+// Each pass runs one wave of CTAs (as many as fit on the SMs: each pass
+// sizes its own grid), each over a contiguous range of whole warps of
+// nodes: the FP64 pipe is per SM, so every SM gets the same number of
+// node-warps (to within one per CTA) and no SM idles while another finishes
+// a second round.  Each pass is launched as a programmatic dependent of the
+// one before it (launch_pdl), so its CTAs take the SMs the previous pass
+// leaves and start as soon as it ends; a grid of exactly the CTAs the SMs
+// hold cannot crowd one SM when it is placed that way.  The per-CTA
+// partials (Lambda, E_M, xi) keep the fused kernel's layout.
 #include "stage_kernels.cuh"
 
 namespace glemur {
-
-struct SplitArgs {
-  int nx, ny, nz;
-  double h2[3];
-  const double* d[2];  // ping-pong displacements
-  const double* B0s;
-  double* k[6];        // k1..k5 (k[5] = optional k6)
-  double* ys[2];       // stage inputs: y_s in ys[s & 1] (s >= 1), 3N each;
-                       // boundary entries hold the fixed boundary positions
-  double* Bb;          // B, 3N
-  double* rb;          // 1/det G, N
-  int diag, force;
-  DevState* st;
-  double* part;
-  int nblocks;
-};
 
 // This CTA's node range: warps [W b / G, W (b+1) / G) of the W = N/32 node
 // warps (rounded up), as node indices [begin, end).
@@ -157,6 +143,16 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
   return zeta * dot3(B, B) * det;
 }
 
+// This CTA's partial of kind `kind`; the slots of the partial stride beyond
+// this launch's grid are zeroed (neutral for the sums and for the maxima of
+// non-negative values), so a pass with fewer CTAs than the stride leaves no
+// stale slot behind.
+__device__ __forceinline__ void put_partial(const SplitArgs& a, int kind, double v) {
+  double* p = a.part + kind * a.nblocks;
+  p[blockIdx.x] = v;
+  for (int b = gridDim.x + blockIdx.x; b < a.nblocks; b += gridDim.x) p[b] = 0.0;
+}
+
 // a.b - c.d as one multiply and five FMAs (one FP64 instruction fewer than
 // two dot products and a subtraction)
 __device__ __forceinline__ double dot3_sub(const double a[3], const double b[3],
@@ -201,17 +197,15 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   }
   pdl_trigger();
   if (energy) {
-    const int bid = blockIdx.x;
     const double v = block_reduce<false>(eacc, red);
-    if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
+    if (threadIdx.x == 0) put_partial(a, PART_E, v);
   }
 }
 
 // Pass C (stage s): current and velocity at interior nodes; k_s and the
 // next stage input, or (s = 5) the update, the error and k6.  Held to 64
-// registers (a few spilled values in two of the stages) so that an SM holds
-// four CTAs of either pass: the grid is then exactly four per SM, and a
-// launch that starts while the previous pass drains cannot crowd one SM.
+// registers (a few spilled values in two of the stages): four CTAs (32
+// warps) per SM instead of three, at no measured cost.
 template <int S>
 __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
   constexpr bool FINAL = S == 5;
@@ -303,36 +297,42 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
     }
   }
   pdl_trigger();
-  const int bid = blockIdx.x;
   if (FINAL) {
     const double v = block_reduce<true>(acc.lam, red);
-    if (threadIdx.x == 0) a.part[PART_LAMBDA * a.nblocks + bid] = v;
+    if (threadIdx.x == 0) put_partial(a, PART_LAMBDA, v);
   }
   if (S == 0 && a.diag) {
     double v = block_reduce<true>(acc.xi2, red);
-    if (threadIdx.x == 0) a.part[PART_XI2 * a.nblocks + bid] = v;
+    if (threadIdx.x == 0) put_partial(a, PART_XI2, v);
     v = block_reduce<true>(acc.xis2, red);
-    if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
+    if (threadIdx.x == 0) put_partial(a, PART_XIS2, v);
   }
 }
 
-// CTAs of 256 threads per SM that both passes can hold at once.
-int split_ctas_per_sm() {
-  int b = 0, c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_split_B<0>, 256, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_split_C<5>, 256, 0);
-  const int m = b < c ? b : c;
-  return m > 0 ? m : 1;
+// CTAs of 256 threads per SM that pass B and pass C of each stage can hold.
+void split_ctas_per_sm(int b[6], int c[6]) {
+  void (*kb[6])(const SplitArgs) = {k_split_B<0>, k_split_B<1>, k_split_B<2>,
+                                    k_split_B<3>, k_split_B<4>, k_split_B<5>};
+  void (*kc[6])(const SplitArgs) = {k_split_C<0>, k_split_C<1>, k_split_C<2>,
+                                    k_split_C<3>, k_split_C<4>, k_split_C<5>};
+  for (int s = 0; s < 6; ++s) {
+    b[s] = c[s] = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[s], kb[s], 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c[s], kc[s], 256, 0);
+    if (b[s] < 1) b[s] = 1;
+    if (c[s] < 1) c[s] = 1;
+  }
 }
 
-// Launch both passes of stage s on `nblocks` CTAs of 256 threads.
+// Launch both passes of stage s (grid_b[s], grid_c[s] CTAs of 256 threads).
 cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s) {
-  const dim3 g(a.nblocks);
+  if (stage < 0 || stage > 5) return cudaErrorInvalidValue;
+  const dim3 gb(a.grid_b[stage]), gc(a.grid_c[stage]);
   cudaError_t e = cudaSuccess;
-#define GLEMUR_SPLIT_CASE(SS)                                   \
-  case SS:                                                      \
-    e = launch_pdl(k_split_B<SS>, g, dim3(256), 0, s, a);       \
-    if (e == cudaSuccess) e = launch_pdl(k_split_C<SS>, g, dim3(256), 0, s, a); \
+#define GLEMUR_SPLIT_CASE(SS)                                                      \
+  case SS:                                                                         \
+    e = launch_pdl(k_split_B<SS>, gb, dim3(256), 0, s, a);                         \
+    if (e == cudaSuccess) e = launch_pdl(k_split_C<SS>, gc, dim3(256), 0, s, a);   \
     break;
   switch (stage) {
     GLEMUR_SPLIT_CASE(0)
