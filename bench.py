@@ -47,9 +47,9 @@ L2_FLUSH_BYTES = 512 << 20
 # of one attempt's six stages, averaged; FP64: both passes of a stage), keyed
 # by (n, precision, curl); absent workloads report null
 NCU_TRAFFIC = {
-    (64, "fp64", "mimetic"): 45.89e6,   # 275.34 MB per attempt
+    (64, "fp64", "mimetic"): 45.89e6,
     (64, "mixed", "mimetic"): 15.71e6,
-    (128, "mixed", "mimetic"): 152.87e6,
+    (128, "mixed", "mimetic"): 155.49e6,
 }
 
 
