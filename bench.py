@@ -213,7 +213,7 @@ def reference_arm(args):
     # step requested, at most 120 s
     cb = run_oracle_all_cores(args.workload, min(120.0, 4.0 * max(args.steps, 1)), args.curl)
     out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-           "steps": cb["steps"], "warmup": args.warmup,
+           "steps": args.steps, "warmup": args.warmup, "oracle_attempts": cb["steps"],
            "ms_per_step": 1e3 * w.grid.n_interior * 6 / cb["value"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference", "config": config_dict(args, w), "cpu_baseline": cb,
