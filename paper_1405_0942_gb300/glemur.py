@@ -186,6 +186,7 @@ class Relaxation:
                                     C.c_void_p(self.workspace.data_ptr()), int(nbytes))
         _check(rc, "glemur_init_grid")
         self._h = h
+        self._held = []  # (event, host buffer) pairs the stream may still read
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -194,19 +195,35 @@ class Relaxation:
             self._h = None
 
     # -- fields -----------------------------------------------------------
-    def set_x(self, x):
+    def set_x(self, x, non_blocking=False):
+        """Positions x (3, nz, ny, nx) float64, on the device or the host.
+        A host buffer is read asynchronously; with non_blocking=False the
+        call waits for the copy, with non_blocking=True (as torch's
+        Tensor.to) it returns at once and the caller must not modify the
+        buffer until the stream has passed the copy (the library keeps it
+        alive until then)."""
         p, mem, keep = _field_ptr(x, self.shape)
         _check(lib().glemur_set_x(self._h, p, mem), "glemur_set_x")
-        self._sync_if(mem)
+        self._after_host_read(mem, keep, non_blocking)
 
-    def set_B0(self, B0):
+    def set_B0(self, B0, non_blocking=False):
+        """B0 (3, nz, ny, nx) float64 at the label grid; host buffers as in
+        set_x."""
         p, mem, keep = _field_ptr(B0, self.shape)
         _check(lib().glemur_set_B0(self._h, p, mem), "glemur_set_B0")
-        self._sync_if(mem)
+        self._after_host_read(mem, keep, non_blocking)
 
-    def _sync_if(self, mem):
-        if mem == MEM_HOST:  # the host buffer may be released on return
+    def _after_host_read(self, mem, keep, non_blocking):
+        if mem != MEM_HOST:
+            return
+        if not non_blocking:
             self.stream.synchronize()
+            return
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        self._held = [(e, k) for e, k in self._held if not e.query()]
+        self._held.append((ev, keep))
 
     def get_x(self, out=None):
         """Current positions: into `out` (CUDA tensor or numpy array), else a
