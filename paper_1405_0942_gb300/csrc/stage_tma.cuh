@@ -308,6 +308,15 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   for (int dd = 0; dd < 6; ++dd) yo[dd] = xslot(k0 + dd - 1) * Gm::YSTRt;
 #pragma unroll
   for (int dd = 0; dd < 4; ++dd) bo[dd] = bslot(k0 + dd - 1) * Gm::BPt;
+  // centre values (d, k_j) of the output nodes, loaded one plane ahead: the
+  // loads for plane m+1 are issued before the barrier that ends plane m
+  Centre<float, float, S> ce[R];
+  {
+    const bool zin0 = k0 >= 1 && k0 <= a.nz - 2;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (zin0 && out_xy[r]) ce[r].issue(a, d, N, k0 * nxy + nxy_out + r * WARPS * a.nx);
+  }
   for (int m = k0; m < k1; ++m) {
     const int it = m - k0;
     const float* yl[6];
@@ -326,10 +335,6 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         tma_load_4d(zr + ((m + 3) & 1) * Gm::ZSTRt, &maps.b0, i0 - 4, j0 - 1, m + 3, 0, bar);
     }
     const bool zin = m >= 1 && m <= a.nz - 2;
-    Centre<float, float, S> ce[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (zin && out_xy[r]) ce[r].issue(a, d, N, m * nxy + nxy_out + r * WARPS * a.nx);
     if (it > 0) {
       const int pi = it - 1;
       const bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
@@ -354,6 +359,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         tma_mimetic_out<Gm, S>(a, ty + r * WARPS, m * nxy + nxy_out + r * WARPS * a.nx, yl[0],
                                yl[1], yl[2], bl[0], bl[1], bl[2], ce[r], dout, an, st, diag,
                                acc);
+    if (m + 1 < k1) {
+      const bool zin1 = m + 1 >= 1 && m + 1 <= a.nz - 2;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (zin1 && out_xy[r])
+          ce[r].issue(a, d, N, (m + 1) * nxy + nxy_out + r * WARPS * a.nx);
+    }
     const int y_first = yo[0], b_first = bo[0];
 #pragma unroll
     for (int dd = 0; dd < 5; ++dd) yo[dd] = yo[dd + 1];
