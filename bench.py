@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 512 << 20
 NCU_TRAFFIC = {
     (64, "fp64", "mimetic"): 45.89e6,
     (64, "mixed", "mimetic"): 15.71e6,
-    (128, "mixed", "mimetic"): 155.49e6,
+    (128, "mixed", "mimetic"): 155.34e6,
 }
 
 
