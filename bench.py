@@ -1,11 +1,12 @@
 """Throughput of the Lagrangian magneto-frictional relaxation step on GB300.
 
-A step is one Cash-Karp attempt of the whole hot path (six fused stage
-kernels -- stage input, Jacobian, pull-back, current, J x B -- the
-fifth-order update with its embedded error, and the step control) over the
-64^3 braid workload (6 twist regions, pre-distorted grid, FP64, mimetic
-current).  Metric: interior node-stage updates per second (6 per interior
-node per attempt).
+A step is one Cash-Karp attempt of the whole hot path (six stages -- stage
+input, Jacobian, pull-back, current, J x B; one fused kernel per stage in
+mixed precision, two passes per stage in FP64 -- the fifth-order update
+with its embedded error, and the step control) over the 64^3 braid
+workload (6 twist regions, pre-distorted grid, FP64, mimetic current),
+timed whole with CUDA events, L2 flushed between steps.  Metric: interior
+node-stage updates per second (6 per interior node per attempt).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
