@@ -257,12 +257,7 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
     u[0] = J[1] * B[2] - J[2] * B[1];
     u[1] = J[2] * B[0] - J[0] * B[2];
     u[2] = J[0] * B[1] - J[1] * B[0];
-    if (S == 0 && a.diag) {
-      const double u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
-      if (gt_nonneg(u2, acc.xi2 * b2 * b2)) acc.xi2 = u2 / (b2 * b2);
-      const double jb = j2 * b2;
-      if (gt_nonneg(jb, 0.0) && gt_nonneg(u2, acc.xis2 * jb) && not_nan(u2)) acc.xis2 = u2 / jb;
-    }
+    if (S == 0 && a.diag) acc.max_xi(dot3(u, u), dot3(B, B), dot3(J, J));
     if (!FINAL) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -303,9 +298,9 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
     if (threadIdx.x == 0) put_partial(a, PART_LAMBDA, v);
   }
   if (S == 0 && a.diag) {
-    double v = block_reduce<true>(acc.xi2, red);
+    double v = block_reduce<true>(acc.xi2(), red);
     if (threadIdx.x == 0) put_partial(a, PART_XI2, v);
-    v = block_reduce<true>(acc.xis2, red);
+    v = block_reduce<true>(acc.xis2(), red);
     if (threadIdx.x == 0) put_partial(a, PART_XIS2, v);
   }
 }

@@ -203,17 +203,41 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
 // maxima in float, so no per-node work lands on the FP64 pipe.
 template <typename C>
 struct Acc;
+//
+// The force-free maxima xi^2 = max |J x B|^2 / |B|^4 and xi'^2 = max
+// |J x B|^2 / (|J|^2 |B|^2): FP64 keeps the largest ratio as its numerator
+// and denominator and compares by cross-multiplication (a > n/d as
+// a d > n b), dividing once per thread at the end -- an FP64 division per
+// node, taken whenever a thread's maximum grows, cost a fifth of the first
+// stage's FP64 work.  (The products overflow only for |B| beyond ~1e50.)
+// FP32 keeps the ratio.
 template <>
 struct Acc<double> {
-  double e = 0.0, lam = 0.0, xi2 = 0.0, xis2 = 0.0;
+  double e = 0.0, lam = 0.0;
+  double xn = 0.0, xd = 1.0, sn = 0.0, sd = 1.0;  // xi^2 = xn / xd, xi'^2 = sn / sd
   int bad = 0;
   __device__ __forceinline__ void add_e(double w) { e += w; }
   __device__ __forceinline__ void max_lam(double v) { lam = nanmax(lam, v); }
   __device__ __forceinline__ double e_total() const { return e; }
+  // one node: u2 = |J x B|^2, b2 = |B|^2, j2 = |J|^2 (NaN u2 propagates)
+  __device__ __forceinline__ void max_xi(double u2, double b2, double j2) {
+    const double b4 = b2 * b2;
+    if (gt_nonneg(u2 * xd, xn * b4)) {
+      xn = u2;
+      xd = b4;
+    }
+    const double jb = j2 * b2;
+    if (gt_nonneg(jb, 0.0) && gt_nonneg(u2 * sd, sn * jb) && not_nan(u2)) {
+      sn = u2;
+      sd = jb;
+    }
+  }
+  __device__ __forceinline__ double xi2() const { return xn / xd; }
+  __device__ __forceinline__ double xis2() const { return sn / sd; }
 };
 template <>
 struct Acc<float> {
-  float eh = 0.0f, el = 0.0f, lam = 0.0f, xi2 = 0.0f, xis2 = 0.0f;
+  float eh = 0.0f, el = 0.0f, lam = 0.0f, x2 = 0.0f, s2 = 0.0f;
   int bad = 0;
   __device__ __forceinline__ void add_e(float w) {
     float s, err;
@@ -223,6 +247,13 @@ struct Acc<float> {
   }
   __device__ __forceinline__ void max_lam(float v) { lam = nanmaxf_(lam, v); }
   __device__ __forceinline__ double e_total() const { return (double)eh + (double)el; }
+  __device__ __forceinline__ void max_xi(float u2, float b2, float j2) {
+    if (gt_nonneg(u2, x2 * b2 * b2)) x2 = u2 / (b2 * b2);
+    const float jb = j2 * b2;
+    if (gt_nonneg(jb, 0.0f) && gt_nonneg(u2, s2 * jb) && not_nan(u2)) s2 = u2 / jb;
+  }
+  __device__ __forceinline__ double xi2() const { return x2; }
+  __device__ __forceinline__ double xis2() const { return s2; }
 };
 
 // ------------------------------------------------------------ x_s planes
@@ -473,11 +504,8 @@ __device__ __forceinline__ void emit_centre(const StageArgs<T>& a, int n, const 
                                             Acc<C>& acc) {
   const int N = a.nx * a.ny * a.nz;
   if (diag) {
-    const C u2 = dot3(u, u), b2 = dot3(B, B), j2 = dot3(J, J);
     // xi^2 = |J x B|^2 / |B|^4 and the sine form |J x B|^2 / (|J|^2 |B|^2)
-    if (gt_nonneg(u2, acc.xi2 * b2 * b2)) acc.xi2 = u2 / (b2 * b2);
-    const C jb = j2 * b2;
-    if (gt_nonneg(jb, (C)0) && gt_nonneg(u2, acc.xis2 * jb) && not_nan(u2)) acc.xis2 = u2 / jb;
+    acc.max_xi(dot3(u, u), dot3(B, B), dot3(J, J));
   }
   if constexpr (S < 5) {
     T* ko = a.k[S];
@@ -567,9 +595,9 @@ __device__ __forceinline__ void write_partials(const StageArgs<T>& a, bool final
   if (diag) {
     double v = block_reduce<false>(acc.e_total(), red);
     if (threadIdx.x == 0) a.part[PART_E * a.nblocks + bid] = v;
-    v = block_reduce<true>((double)acc.xi2, red);
+    v = block_reduce<true>(acc.xi2(), red);
     if (threadIdx.x == 0) a.part[PART_XI2 * a.nblocks + bid] = v;
-    v = block_reduce<true>((double)acc.xis2, red);
+    v = block_reduce<true>(acc.xis2(), red);
     if (threadIdx.x == 0) a.part[PART_XIS2 * a.nblocks + bid] = v;
   }
 }
