@@ -21,6 +21,9 @@
 //      nodes whose difference stencils contain it (central inside, one-sided
 //      on boundary faces).
 // Boundary nodes are line-tied: their position adjoint is not propagated.
+// Every kernel here is launched as a programmatic dependent of the one
+// before it (launch_pdl) and starts with pdl_wait(), before any memory
+// access.
 #include <cuda_runtime.h>
 
 #include <climits>
