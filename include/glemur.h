@@ -24,7 +24,12 @@
  * Memory.  The library never allocates device memory.  The caller passes a
  * device workspace of at least glemur_workspace_bytes() bytes (for example
  * a torch.uint8 tensor) and keeps it alive until glemur_destroy().  Host
- * pointers passed with GLEMUR_MEM_HOST may be pageable or pinned.
+ * pointers passed with GLEMUR_MEM_HOST may be pageable or pinned: pageable
+ * buffers go through a device staging buffer, page-locked ones are read
+ * (glemur_set_x, glemur_set_B0) or written (glemur_get_x, glemur_velocity)
+ * in place by the conversion kernels.  An input buffer is read
+ * asynchronously on the stream; the caller keeps it unchanged until the
+ * stream has passed the call.  Output calls synchronise the stream.
  *
  * Streams.  All device work runs on the cudaStream_t given to
  * glemur_init_grid (NULL = the legacy default stream).  Calls that return
@@ -139,6 +144,10 @@ size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
  *   GLEMUR_TEST_TMA_TIMEOUT=1  test hook: every TMA tile wait expects 16
  *                         bytes that never arrive, so the bounded wait gives
  *                         up and steps fail with GLEMUR_ERR_TIMEOUT
+ * and, read at each call with a host buffer:
+ *   GLEMUR_HOST_STAGING=1 copy page-locked host buffers through the staging
+ *                         buffer instead of reading and writing them in
+ *                         place from the conversion kernels
  * and, read once per process, for every launch of the library:
  *   GLEMUR_PDL=0          ordinary kernel launches instead of programmatic
  *                         dependent launches (each kernel of an attempt or

@@ -577,6 +577,19 @@ int reset_state(glemur_ctx* c) {
 
 // Source pointer of an input field: the caller's device pointer, or the
 // staging buffer after an H2D copy.
+// The device's address of a page-locked host buffer (mapped into the
+// device address space), else null: the conversion kernels then read and
+// write it in place over the host link instead of through a staging copy.
+double* mapped_host(const void* p) {
+  if (getenv("GLEMUR_HOST_STAGING")) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // not a pointer the runtime knows: pageable memory
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? (double*)at.devicePointer : nullptr;
+}
+
 int stage_in(glemur_ctx* c, const double* src, int mem, const double** dev) {
   if (!src) return GLEMUR_ERR_BADARG;
   if (mem == GLEMUR_MEM_DEVICE) {
@@ -584,16 +597,30 @@ int stage_in(glemur_ctx* c, const double* src, int mem, const double** dev) {
     return GLEMUR_OK;
   }
   if (mem != GLEMUR_MEM_HOST) return GLEMUR_ERR_BADARG;
+  if (const double* m = mapped_host(src)) {
+    *dev = m;
+    return GLEMUR_OK;
+  }
   cudaError_t e = cudaMemcpyAsync(c->stage, src, sizeof(double) * 3 * c->N,
                                   cudaMemcpyHostToDevice, c->s);
   *dev = c->stage;
   return cuda_rc(e);
 }
 
-int stage_out(glemur_ctx* c, double* dst, int mem) {
+// Where a conversion kernel writes a host-bound result: the caller's buffer
+// (device memory, or page-locked host memory mapped into the device), else
+// the staging buffer that stage_out copies from.
+double* out_target(glemur_ctx* c, double* dst, int mem) {
+  if (mem == GLEMUR_MEM_DEVICE) return dst;
+  double* m = mapped_host(dst);
+  return m ? m : c->stage;
+}
+
+int stage_out(glemur_ctx* c, double* dst, double* written, int mem) {
   if (mem == GLEMUR_MEM_DEVICE) return GLEMUR_OK;
-  cudaError_t e = cudaMemcpyAsync(dst, c->stage, sizeof(double) * 3 * c->N,
-                                  cudaMemcpyDeviceToHost, c->s);
+  cudaError_t e = cudaSuccess;
+  if (written == c->stage)
+    e = cudaMemcpyAsync(dst, c->stage, sizeof(double) * 3 * c->N, cudaMemcpyDeviceToHost, c->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
   return cuda_rc(e);
 }
@@ -928,7 +955,7 @@ int glemur_set_B0(glemur_ctx* c, const double* B0, int mem) {
 
 int glemur_get_x(glemur_ctx* c, double* x, int mem) {
   if (!c || !x || (mem != GLEMUR_MEM_DEVICE && mem != GLEMUR_MEM_HOST)) return GLEMUR_ERR_BADARG;
-  double* dst = mem == GLEMUR_MEM_DEVICE ? x : c->stage;
+  double* dst = out_target(c, x, mem);
   const int nb = elementwise_blocks(c->N);
   if (c->o.precision == GLEMUR_MIXED)
     k_get_x<float><<<nb, 256, 0, c->s>>>(geom(c), (const float* const*)c->dbuf_dev, c->st, dst);
@@ -937,14 +964,14 @@ int glemur_get_x(glemur_ctx* c, double* x, int mem) {
                                           dst);
   int rc = cuda_rc(cudaGetLastError());
   if (rc) return rc;
-  return stage_out(c, x, mem);
+  return stage_out(c, x, dst, mem);
 }
 
 int glemur_velocity(glemur_ctx* c, double* u, int mem) {
   if (!c || !u || (mem != GLEMUR_MEM_DEVICE && mem != GLEMUR_MEM_HOST)) return GLEMUR_ERR_BADARG;
   cudaError_t e = launch_stage(c, c->o.curl, 0, 0, 1);
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
-  double* dst = mem == GLEMUR_MEM_DEVICE ? u : c->stage;
+  double* dst = out_target(c, u, mem);
   const long long M = 3 * c->N;
   if (c->o.precision == GLEMUR_MIXED)
     k_to_f64<float><<<elementwise_blocks(M), 256, 0, c->s>>>(M, (const float*)c->k[0], dst);
@@ -952,7 +979,7 @@ int glemur_velocity(glemur_ctx* c, double* u, int mem) {
     k_to_f64<double><<<elementwise_blocks(M), 256, 0, c->s>>>(M, (const double*)c->k[0], dst);
   int rc = cuda_rc(cudaGetLastError());
   if (rc) return rc;
-  return stage_out(c, u, mem);
+  return stage_out(c, u, dst, mem);
 }
 
 int glemur_attempts(glemur_ctx* c, int n_attempts) {
