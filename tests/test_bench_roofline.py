@@ -1,0 +1,51 @@
+"""The benchmark's roofline arithmetic on synthetic timings (no GPU):
+achieved = algorithmic bytes (FP64: flops) of the six stage launches over
+the whole-attempt time, frac = achieved / peak, stage shares from the
+event-separated split."""
+import numpy as np
+
+import bench
+
+
+class _G:
+    def __init__(self, n):
+        self.nx = self.ny = self.nz = n
+        self.n_interior = (n - 2) ** 3
+
+
+class _W:
+    def __init__(self, n):
+        self.grid = _G(n)
+
+
+def test_mixed_roofline_is_bytes_over_whole_attempt():
+    w = _W(128)
+    whole = np.array([0.35, 0.35])                     # ms per attempt
+    split = np.array([[0.06] * 6 + [0.01]] * 2)        # six stages + control
+    r = bench.roofline_entry(whole, split, w, "mixed", "mimetic", 6783.8, "measured")
+    I = 126 ** 3
+    gbs = 66.0 * I * 6 / (0.35e-3) / 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert np.isclose(r["achieved"], gbs) and np.isclose(r["frac"], gbs / 6783.8)
+    assert r["algorithmic_bytes_per_launch"] == 66.0 * I
+    assert r["traffic"] == bench.NCU_TRAFFIC[(128, "mixed", "mimetic")]
+    assert np.isclose(sum(r["stage_shares"]), 0.36 / 0.37, atol=1e-3)
+
+
+def test_fp64_roofline_is_flops_against_the_fp64_rate():
+    w = _W(64)
+    whole = np.array([0.4])
+    split = np.array([[0.07] * 6 + [0.01]])
+    r = bench.roofline_entry(whole, split, w, "fp64", "mimetic", 6783.8, "measured")
+    I = 62 ** 3
+    tf = bench.ALGO_FLOPS_F64["mimetic"] * I * 6 / 0.4e-3 / 1e12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert np.isclose(r["achieved"], tf)
+    assert np.isclose(r["frac"], tf * 1e12 / bench.FP64_PEAK_FLOPS)
+    assert np.isclose(r["hbm_achieved_gbs"], 132.0 * I * 6 / 0.4e-3 / 1e9)
+
+
+def test_workload_without_a_capture_reports_null_traffic():
+    r = bench.roofline_entry(np.array([1.0]), np.array([[0.1] * 7]), _W(96), "mixed",
+                             "direct", 6783.8, "measured")
+    assert r["traffic"] is None
