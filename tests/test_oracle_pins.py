@@ -187,6 +187,43 @@ def test_flux_converges_second_order_on_smooth_map():
 
 
 @pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
+def test_forcefree_closed_form_for_a_sheared_field(curl):
+    """x = X and B0 = (0, x, 1): J = curl B0 = (0, 0, 1) exactly (linear
+    field), J x B = (-x, 0, 0), so xi = max |x| / (x^2 + 1) and the sine form
+    max |x| / sqrt(x^2 + 1) over the interior nodes (section "Evolution of
+    Diagnostic Parameters"); on 9 nodes per axis the interior reaches
+    |x| = 3/4: 0.48 and 0.6."""
+    g = gi.Grid(9, 9, 9)
+    X = gi.nodes(g)
+    B0 = np.stack([np.zeros_like(X[0]), X[0].copy(), np.ones_like(X[0])])
+    xi, xis, rc = ora.forcefree(g, X, B0, curl)
+    assert rc == ora.OK
+    assert abs(xi - 0.48) < 1e-13 and abs(xis - 0.6) < 1e-13
+
+
+@pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
+def test_forcefree_of_the_quadratic_field_is_the_interior_maximum(curl):
+    """x = X and B0 = (y^2, z^2, x^2), J = (-2z, -2x, -2y) exactly: the
+    oracle's xi and sine form equal the maxima of |J x B| / |B|^2 and
+    |J x B| / (|J| |B|) over the interior nodes, formed here from the closed
+    forms (boundary nodes, where |B| may vanish, excluded)."""
+    g = gi.Grid(9, 8, 10)
+    X = gi.nodes(g)
+    B0 = np.stack([X[1] ** 2, X[2] ** 2, X[0] ** 2])
+    J = np.stack([-2 * X[2], -2 * X[0], -2 * X[1]])
+    f = np.linalg.norm(np.cross(J, B0, axis=0), axis=0)
+    b = np.linalg.norm(B0, axis=0)
+    j = np.linalg.norm(J, axis=0)
+    inner = (slice(1, -1),) * 3
+    xi_ex = (f / b ** 2)[inner].max()
+    jb = (j * b)[inner]
+    xis_ex = (f[inner][jb > 1e-300] / jb[jb > 1e-300]).max()
+    xi, xis, rc = ora.forcefree(g, X, B0, curl)
+    assert rc == ora.OK
+    assert abs(xi - xi_ex) < 1e-11 * xi_ex and abs(xis - xis_ex) < 1e-11 * xis_ex
+
+
+@pytest.mark.parametrize("curl", [ora.MIMETIC, ora.DIRECT])
 def test_current_exact_for_quadratic_field_on_uniform_grid(curl):
     """x = X and the solenoidal quadratic B0 = (y^2, z^2, x^2): central
     differences are exact for quadratics, so J = curl B0 = (-2z, -2x, -2y)."""
