@@ -26,6 +26,19 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_environment_switch_is_documented():
+    """Each GLEMUR_* variable the library reads is described in the header."""
+    csrc = os.path.join(ROOT, "paper_1405_0942_gb300", "csrc")
+    used = set()
+    for fn in os.listdir(csrc):
+        if fn.endswith((".cu", ".cuh")):
+            used |= set(re.findall(r'getenv\("(GLEMUR_[A-Z0-9_]+)"\)',
+                                   open(os.path.join(csrc, fn)).read()))
+    header = open(os.path.join(ROOT, "include", "glemur.h")).read()
+    assert used, "no switches found"
+    assert not [v for v in sorted(used) if v + "=" not in header]
+
+
 def test_library_exports_every_declared_symbol():
     from paper_1405_0942_gb300 import build
     path = build.build()
