@@ -141,9 +141,11 @@ size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
  *                         recomputation) instead of the two-pass stages
  *   GLEMUR_KZ=k           z-planes per CTA of the stage kernels instead of
  *                         the cost model's choice
- *   GLEMUR_TEST_TMA_TIMEOUT=1  test hook: every TMA tile wait expects 16
- *                         bytes that never arrive, so the bounded wait gives
- *                         up and steps fail with GLEMUR_ERR_TIMEOUT
+ *   GLEMUR_TEST_TMA_TIMEOUT=1 or 2  test hook: the TMA stage kernels' first
+ *                         tile wait (1) or first wait inside their plane loop
+ *                         (2, CTAs of at least two z-planes) also waits on a
+ *                         barrier that no copy completes, so the bounded wait
+ *                         gives up and steps fail with GLEMUR_ERR_TIMEOUT
  * and, read at each call with a host buffer:
  *   GLEMUR_HOST_STAGING=1 copy page-locked host buffers through the staging
  *                         buffer instead of reading and writing them in
@@ -224,6 +226,20 @@ int glemur_energy(glemur_ctx* ctx, double* E);
  * with the context's current.  Synchronises. */
 int glemur_forcefree_err(glemur_ctx* ctx, double* xi, double* xi_sin);
 
+/* Accepted step sizes kept on the device: the last GLEMUR_DT_LOG accepted
+ * steps since glemur_set_x / glemur_set_state (a ring in the workspace,
+ * written by the device-side step control, so recording a schedule costs no
+ * host synchronisation per step). */
+#define GLEMUR_DT_LOG 65536
+
+/* Copy the sizes of accepted steps first .. first+count-1 (numbered from 0
+ * since glemur_set_x or glemur_set_state) into host memory dts[count], in
+ * order: the step-size schedule of section "Time Stepping"'s control, for
+ * replaying a run with glemur_step_fixed (parity checks, the adjoint).
+ * BADARG if some of those steps have not been accepted yet or have left the
+ * ring (first < accepted - GLEMUR_DT_LOG).  Synchronises. */
+int glemur_get_dt_schedule(glemur_ctx* ctx, long long first, int count, double* dts);
+
 /* Counters and last-attempt values (see glemur_stats).  Synchronises. */
 int glemur_get_stats(glemur_ctx* ctx, glemur_stats* stats);
 
@@ -293,9 +309,12 @@ int glemur_param_contract(int n_params, long long m_len, const double* dB0, cons
  * doubles (512 KiB) that every GPU loading this library holds until the
  * process exits; grids of more than GLEMUR_STATIC_MAX_NODES nodes return
  * GLEMUR_ERR_TOO_LARGE.  The first call on each device resolves that
- * array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (different streams or threads) race.  Asynchronous on `stream` (a
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * the address belongs to the CUDA context that is current then, and a later
+ * call from another context (after cudaDeviceReset, or from a framework's
+ * own non-primary context) resolves it again.  Make the first call from
+ * each context before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams or threads) race.  Asynchronous on `stream` (a
  * cudaStream_t or NULL).  Errors: BADARG, TOO_LARGE, CUDA. */
 int glemur_energy_static(int nx, int ny, int nz, const double lo[3],
                          const double hi[3], const double* x, const double* B0,

@@ -10,6 +10,7 @@
 // shares that array: each CTA overwrites its own slot before the final sum
 // reads it, so nothing has to be cleared, but calls that overlap on the GPU
 // (other streams, other threads) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,9 +27,31 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_energy_partials[kMaxBlocks];
 
-// Address of g_energy_partials on each device, resolved once per device.
+// Address of g_energy_partials on each device, resolved once per device and
+// context: a device address belongs to the context it was resolved in, so a
+// call from another context (after cudaDeviceReset, or from a framework's
+// own non-primary context) resolves it again.
 std::mutex g_mutex;
 double* g_scratch[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link against
+// the driver library); null if the driver does not provide it.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  }
+  return fn;
+}
 
 struct Geom {
   int nx, ny, nz;
@@ -117,17 +140,25 @@ __global__ void k_energy_finalize(const double* partials, long long nb, double s
   }
 }
 
-// Resolve the static scratch's device address for the current device.
+// Resolve the static scratch's device address for the current device and
+// context (cudaGetSymbolAddress with that device current).
 int scratch_for_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GLEMUR_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return GLEMUR_ERR_BADARG;
+  CtxGetCurrentFn get_ctx = ctx_get_current();
+  if (!get_ctx) return GLEMUR_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
+  CUcontext ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS) return GLEMUR_ERR_CUDA;
+  if (!g_scratch[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     double* p = nullptr;
     if (cudaGetSymbolAddress((void**)&p, g_energy_partials) != cudaSuccess || !p)
       return GLEMUR_ERR_CUDA;
+    // the runtime made its context current if there was none
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return GLEMUR_ERR_CUDA;
     g_scratch[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch[dev];
   return GLEMUR_OK;

@@ -186,7 +186,7 @@ bool pdl_enabled() {
   return on;
 }
 
-__global__ void k_control(DevState* st, const double* part, int nb, int diag) {
+__global__ void k_control(DevState* st, const double* part, int nb, int diag, double* dtlog) {
   pdl_trigger();
   pdl_wait();
   if (st->status != ST_OK || st->n_accept >= st->target) return;
@@ -255,6 +255,8 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag) {
     } else {
       if (replay) st->replay = 0;
       if (accept) {
+        // the step-size log: accepted step n_acc in slot n_acc mod the ring
+        dtlog[n_acc % GLEMUR_DT_LOG] = dt;
         st->dt_last = dt;
         st->t = t + dt;
         st->cur = cur ^ 1;
@@ -352,9 +354,10 @@ struct glemur_ctx {
   double* stage;    // 3N doubles for host transfers
   double* part;     // NPART * max_blocks
   DevState* st;
+  double* dtlog;    // ring of GLEMUR_DT_LOG accepted step sizes
   int split;                             // FP64 mimetic stages in two passes
   int tma;                               // mixed mimetic stages with TMA tiles
-  unsigned tma_test_extra;               // test hook: unsatisfiable tile wait
+  int tma_test;                          // test hook: unsatisfiable tile wait
   TmaMaps maps;                          // their tensor maps
   void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
@@ -371,7 +374,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field, stage, part, state, ptrs, split, total;
+  size_t field, stage, part, state, ptrs, dtlog, split, total;
   int max_blocks;
 };
 
@@ -391,12 +394,13 @@ Layout layout(int nx, int ny, int nz, int precision) {
   L.part = align256((size_t)NPART * L.max_blocks * sizeof(double));
   L.state = align256(sizeof(DevState));
   L.ptrs = 256;
+  L.dtlog = align256((size_t)GLEMUR_DT_LOG * sizeof(double));
   // two stage inputs (mimetic stages); FP64 also B and 1/det G for the
   // two-pass stages
   L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
                                                           align256((size_t)N * 8)
                                                     : 0);
-  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.split;
+  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.split;
   return L;
 }
 
@@ -468,7 +472,7 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
-  a.tma_test_extra = c->tma_test_extra;
+  a.tma_test = c->tma_test;
   return a;
 }
 
@@ -535,7 +539,7 @@ cudaError_t launch_attempt(const glemur_ctx* c) {
     if (e != cudaSuccess) return e;
   }
   return launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
-                    nblocks_of(c, c->o.curl), diag);
+                    nblocks_of(c, c->o.curl), diag, c->dtlog);
 }
 
 int read_state(glemur_ctx* c, DevState* hs) {
@@ -820,6 +824,7 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->part = (double*)p; p += L.part;
   c->st = (DevState*)p; p += L.state;
   c->dbuf_dev = (void**)p; p += L.ptrs;
+  c->dtlog = (double*)p; p += L.dtlog;
   c->max_blocks = L.max_blocks;
   c->split = 0;
   c->ys[0] = c->ys[1] = c->Bb = c->rb = nullptr;
@@ -838,11 +843,12 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   const bool mixed = o.precision == GLEMUR_MIXED;
   if (e == cudaSuccess) e = mixed ? prepare_f32_mimetic() : prepare_f64_mimetic();
   c->tma = 0;
-  // GLEMUR_TEST_TMA_TIMEOUT=1 makes every TMA prologue wait for 16 bytes that
-  // never arrive, so that tests can exercise the bounded wait and the
-  // GLEMUR_ERR_TIMEOUT status without any fault
+  // GLEMUR_TEST_TMA_TIMEOUT=1 (2) makes the TMA prologue wait (the first
+  // wait inside the plane loop) also wait on a barrier that never completes,
+  // so that tests can exercise the bounded wait and the GLEMUR_ERR_TIMEOUT
+  // status without any fault
   const char* tt = getenv("GLEMUR_TEST_TMA_TIMEOUT");
-  c->tma_test_extra = tt && atoi(tt) > 0 ? 16u : 0u;
+  c->tma_test = tt && (atoi(tt) == 1 || atoi(tt) == 2) ? atoi(tt) : 0;
   if (e == cudaSuccess && setup_tma(c)) {
     e = prepare_f32_mimetic_tma();
     c->tma = 1;
@@ -1063,6 +1069,26 @@ int glemur_forcefree_err(glemur_ctx* c, double* xi, double* xi_sin) {
   return GLEMUR_OK;
 }
 
+int glemur_get_dt_schedule(glemur_ctx* c, long long first, int count, double* dts) {
+  if (!c || !dts || first < 0 || count < 0 || count > GLEMUR_DT_LOG) return GLEMUR_ERR_BADARG;
+  DevState hs;
+  int rc = read_state(c, &hs);
+  if (rc) return rc;
+  // the range must have been accepted and still be held by the ring
+  if (first + count > hs.n_accept || first < hs.n_accept - GLEMUR_DT_LOG) return GLEMUR_ERR_BADARG;
+  if (count == 0) return GLEMUR_OK;
+  // at most two contiguous pieces of the ring
+  const int s0 = (int)(first % GLEMUR_DT_LOG);
+  const int n0 = count < GLEMUR_DT_LOG - s0 ? count : GLEMUR_DT_LOG - s0;
+  cudaError_t e = cudaMemcpyAsync(dts, c->dtlog + s0, sizeof(double) * n0,
+                                  cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess && n0 < count)
+    e = cudaMemcpyAsync(dts + n0, c->dtlog, sizeof(double) * (count - n0),
+                        cudaMemcpyDeviceToHost, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  return cuda_rc(e);
+}
+
 int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
   if (!c || !stats) return GLEMUR_ERR_BADARG;
   DevState hs;
@@ -1096,7 +1122,7 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
   if (e == cudaSuccess) {
     e = launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
-                   nblocks_of(c, c->o.curl), diag);
+                   nblocks_of(c, c->o.curl), diag, c->dtlog);
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->s);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);

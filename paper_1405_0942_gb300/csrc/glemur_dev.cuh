@@ -103,9 +103,11 @@ struct StageArgs {
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;
-  // bytes the TMA prologue waits for beyond its loads: 0, or > 0 only to
-  // test the bounded wait (the wait then gives up and the attempt fails)
-  unsigned tma_test_extra;
+  // test hook of the bounded tile waits: 0 (off); 1 or 2 make the TMA
+  // stage kernels also wait, at the prologue (1) or at the first wait
+  // inside the plane loop (2), on a barrier that no copy completes, so that
+  // wait gives up and the attempt fails without any fault
+  int tma_test;
 };
 
 // Programmatic dependent launch.  The kernels of an attempt are launched

@@ -224,7 +224,14 @@ __device__ __forceinline__ void tma_load_B0(const StageArgs<float>& a, int q,
 // boxes of y plane m+4 and B0 plane m+3; every thread waits for the boxes
 // issued in iteration m-1 (y plane m+3, B0 plane m+2), forms B at plane m+2
 // and the current at its R nodes of plane m.  The prologue's boxes complete
-// on a third barrier.  Every wait is bounded (FLAG_TIMEOUT).
+// on a third barrier.  Every wait is bounded: a wait that gives up raises
+// FLAG_TIMEOUT, and thread 0 then waits (bounded again) for every box the
+// CTA still has in flight -- those of the barrier that timed out and of the
+// current iteration -- before the CTA returns.  After a real stall that
+// second wait can give up too: it then only delays the exit.  The test
+// hook (a.tma_test) adds a fourth barrier that no copy completes to the
+// prologue wait (1) or to the first wait inside the loop (2); the real
+// copies do complete, so the clean-up waits see them land.
 template <int WARPS, int R, int S, int MINB>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   if (st->flags & FLAG_TIMEOUT) return;  // an earlier stage of this attempt gave up
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[32];
-  __shared__ uint64_t bars[3];
+  __shared__ uint64_t bars[4];
   unsigned char* base =
       smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // 128-byte aligned
   float* yr = reinterpret_cast<float*>(base);                          // [XRING][YSTRt]
@@ -266,15 +273,17 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   }
   const int nxy_out = (j0 + ty) * a.nx + gi;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
     fence_barrier_init();
+    // test hook: a phase that waits for 16 bytes no copy delivers
+    if (a.tma_test) mbar_arrive_expect_tx(&bars[3], 16u);
     // prologue boxes: input planes k0-2 .. k0+3, B0 of plane k0+2
     unsigned bytes = 0;
     for (int q = k0 - 2; q <= k0 + 3; ++q)
       if (q >= 0 && q < a.nz && q <= k1 + 1) bytes += Gm::YBYTESt;
     const bool z2 = k0 + 2 < a.nz && k0 + 2 <= k1;
     if (z2) bytes += Gm::ZBYTESt;
-    mbar_arrive_expect_tx(&bars[2], bytes + a.tma_test_extra);
+    mbar_arrive_expect_tx(&bars[2], bytes);
     for (int q = k0 - 2; q <= k0 + 3; ++q)
       if (q >= 0 && q < a.nz && q <= k1 + 1)
         tma_load_4d(yr + xslot(q) * Gm::YSTRt, ymap, i0 - 4, j0 - 2, q, 0, &bars[2]);
@@ -283,12 +292,16 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
                   &bars[2]);
   }
   __syncthreads();
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[2], 0))) {
-    if (threadIdx.x == 0) {
-      atomicOr(&a.st->flags, FLAG_TIMEOUT);
-      mbar_wait_bounded(&bars[2], 0);  // boxes still in flight
+  {
+    bool ok = mbar_wait_bounded(&bars[2], 0);
+    if (a.tma_test == 1) ok = ok && mbar_wait_bounded(&bars[3], 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&a.st->flags, FLAG_TIMEOUT);
+        mbar_wait_bounded(&bars[2], 0);  // the prologue's boxes still in flight
+      }
+      return;
     }
-    return;
   }
   for (int q = k0 - 1; q <= k0 + 1; ++q)
     if (q >= 0 && q < a.nz && q <= k1) {
@@ -337,11 +350,14 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     const bool zin = m >= 1 && m <= a.nz - 2;
     if (it > 0) {
       const int pi = it - 1;
-      const bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
+      bool ok = mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
+      if (a.tma_test == 2 && it == 1) ok = ok && mbar_wait_bounded(&bars[3], 0);
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           atomicOr(&a.st->flags, FLAG_TIMEOUT);
-          // let this iteration's boxes land before the CTA leaves
+          // let the boxes of the barrier that gave up and of this
+          // iteration land before the CTA leaves
+          mbar_wait_bounded(&bars[pi & 1], (pi >> 1) & 1);
           mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1);
         }
         return;

@@ -56,7 +56,8 @@ EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
            "glemur_profile_attempt", "glemur_energy_static", "glemur_destroy",
            "glemur_strerror", "glemur_adjoint_workspace_bytes", "glemur_vjp_step",
            "glemur_loss_grad", "glemur_param_contract", "glemur_state_bytes",
-           "glemur_get_state", "glemur_set_state"]
+           "glemur_get_state", "glemur_set_state", "glemur_get_dt_schedule"]
+DT_LOG = 65536  # accepted step sizes the device keeps (GLEMUR_DT_LOG)
 LOSS_ENERGY, LOSS_XI = 0, 1
 
 _lib = None
@@ -95,6 +96,7 @@ def lib() -> C.CDLL:
     L.glemur_energy.argtypes = [vp, dp]
     L.glemur_forcefree_err.argtypes = [vp, dp, dp]
     L.glemur_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.glemur_get_dt_schedule.argtypes = [vp, C.c_longlong, ip, dp]
     L.glemur_kernels_per_attempt.argtypes = [vp]
     L.glemur_profile_attempt.argtypes = [vp, C.POINTER(C.c_float), ip]
     L.glemur_energy_static.argtypes = [ip, ip, ip, dp, dp, vp, vp, vp, vp]
@@ -261,6 +263,15 @@ class Relaxation:
             _check(rc, "glemur_step_fixed")
         return st.as_dict()
 
+    def dt_schedule(self, first, count):
+        """Sizes of accepted steps first .. first+count-1 since set_x, as
+        recorded on the device by the step control (numpy float64)."""
+        out = np.empty(int(count), dtype=np.float64)
+        _check(lib().glemur_get_dt_schedule(self._h, int(first), int(count),
+                                            out.ctypes.data_as(C.POINTER(C.c_double))),
+               "glemur_get_dt_schedule")
+        return out
+
     def stats(self):
         st = Stats()
         _check(lib().glemur_get_stats(self._h, C.byref(st)), "glemur_get_stats")
@@ -355,12 +366,16 @@ def param_contract(dB0, mu):
 
 def relax_with_schedule(relax, x0, n_steps):
     """Run n_steps error-controlled steps from x0 and return the accepted
-    step sizes (the schedule the adjoint replays)."""
+    step sizes (the schedule the adjoint replays), read from the device's
+    step-size log once per DT_LOG steps rather than once per step."""
     relax.set_x(x0)
     dts = []
-    for _ in range(n_steps):
-        st = relax.step(1)
-        dts.append(st["dt_last"])
+    done = 0
+    while done < n_steps:
+        chunk = min(n_steps - done, DT_LOG)
+        relax.step(chunk)
+        dts.extend(float(v) for v in relax.dt_schedule(done, chunk))
+        done += chunk
     return dts
 
 

@@ -1,10 +1,12 @@
 """Failure detection on the GPU without a fault: the mixed-precision
 mimetic stages wait for their TMA tiles on shared-memory barriers with a
-time limit.  GLEMUR_TEST_TMA_TIMEOUT=1 makes each tile wait expect 16 bytes
-that no copy delivers, so the wait gives up (after half a second), the
-kernel raises a flag, lets its own copies land and returns, and the step
-control turns the flag into GLEMUR_ERR_TIMEOUT.  The device stays usable:
-a context created afterwards without the hook matches the oracle."""
+time limit.  GLEMUR_TEST_TMA_TIMEOUT=1 makes the prologue's tile wait also
+wait on a barrier that no copy completes (=2: the first wait inside the
+plane loop, which needs CTAs of at least two z-planes), so the wait gives
+up after half a second; the kernel raises a flag, lets its own copies land
+and returns, and the step control turns the flag into GLEMUR_ERR_TIMEOUT.
+The device stays usable: a context created afterwards without the hook
+matches the oracle."""
 import time
 
 import numpy as np
@@ -40,9 +42,12 @@ def make(G, g, x0, B0):
     return r
 
 
-def test_tile_wait_timeout_is_reported(G, monkeypatch):
+@pytest.mark.parametrize("where", ["1", "2"], ids=["prologue", "plane-loop"])
+def test_tile_wait_timeout_is_reported(G, monkeypatch, where):
     g, x0, B0 = case()
-    monkeypatch.setenv("GLEMUR_TEST_TMA_TIMEOUT", "1")
+    monkeypatch.setenv("GLEMUR_TEST_TMA_TIMEOUT", where)
+    # four z-planes per CTA, so every CTA reaches the loop's first wait
+    monkeypatch.setenv("GLEMUR_KZ", "4")
     r = make(G, g, x0, B0)
     t0 = time.time()
     with pytest.raises(G.GlemurError) as err:
@@ -56,6 +61,7 @@ def test_tile_wait_timeout_is_reported(G, monkeypatch):
         r.step(1)
     del r
     monkeypatch.delenv("GLEMUR_TEST_TMA_TIMEOUT")
+    monkeypatch.delenv("GLEMUR_KZ")
     r2 = make(G, g, x0, B0)
     u = r2.velocity().cpu().numpy()
     u_ref, _ = ora.velocity(g, x0, B0, 0)

@@ -90,6 +90,35 @@ def test_current_exact_on_affine_map(seed, curl):
     assert np.all(Jb == 0)
 
 
+def test_loops_at_a_node_on_affine_map():
+    """ora_mimetic_loops_at on x = A X + t, B0 = b + G X: the loop through the
+    in-plane neighbours +-e_p, +-e_q of surface r = (jk, ki, ij) is the image
+    of a diamond with diagonals 2 h_p e_p and 2 h_q e_q, so its vector area
+    is 2 h_p h_q (A e_p) x (A e_q) = 2 h_p h_q det(A) A^-T e_r (row r of M);
+    the trapezoid edge integrals of the affine B are exact, so the
+    circulations are c = M J with J = curl_x B; and J agrees with
+    ora_curl_mimetic at the node."""
+    g, X, x, B0, A, G, b = affine_case(5)
+    L = A @ G @ np.linalg.inv(A) / np.linalg.det(A)
+    Jex = np.array([L[2, 1] - L[1, 2], L[0, 2] - L[2, 0], L[1, 0] - L[0, 1]])
+    B, _, _ = ora.pullback(g, x, B0)
+    Jall, _, _ = ora.curl_mimetic(g, x, B)
+    cof = np.linalg.det(A) * np.linalg.inv(A).T
+    h = g.h
+    for (i, j, k) in [(1, 1, 1), (3, 4, 2), (5, 6, 7)]:
+        c, M, J, rc = ora.mimetic_loops_at(g, x, B, i, j, k)
+        assert rc == ora.OK
+        for r in range(3):
+            p, q = (r + 1) % 3, (r + 2) % 3
+            area = 2.0 * h[p] * h[q] * cof[:, r]
+            assert np.abs(M[r] - area).max() <= 1e-13 * np.abs(area).max()
+        assert np.abs(c - M @ Jex).max() <= 1e-12 * np.abs(M).max() * np.abs(Jex).max()
+        assert np.abs(J - Jex).max() <= 1e-11 * np.abs(L).max()
+        assert np.array_equal(J, Jall[:, k, j, i])
+    # boundary nodes have no loops
+    assert ora.mimetic_loops_at(g, x, B, 0, 2, 2)[3] == ora.ERR_BADARG
+
+
 def test_flux_through_closed_cells_vanishes_on_affine_map():
     """B = F B0 / Delta is the push-forward of a solenoidal field: the net
     flux out of every deformed (parallelepiped) cell is zero to rounding, and

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import glemur_inputs as gi
+import oracle as ora
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,33 @@ def test_energy_static_matches_energy_twice(L, dims):
         assert _energy_static(L, g, x_dev, B0_dev, E_dev) == 0
         E = float(E_dev.item())
         assert abs(E - E_ref) < 1e-13 * E_ref, (E, E_ref)
+
+
+def test_energy_static_matches_oracle_and_allocates_nothing(L):
+    """The entry point's own Jacobian and energy kernels against the FP64
+    oracle's eq. "magnetic energy" (1e-13 relative), on a ragged grid with
+    a pre-distorted interior; after a first call (which may load the
+    library's device code), further calls leave the device's free memory
+    unchanged."""
+    g = gi.Grid(37, 21, 26)
+    X = gi.nodes(g)
+    x0 = gi.predistort(X, 4) + 0.01 * np.sin(2.0 * X[[1, 2, 0]])
+    B0 = gi.braid_field(X, gi.braid_regions(6, 7, False)) + 0.1 * gi.abc_field(X)
+    E_ref, rc = ora.energy(g, x0, B0)
+    assert rc == ora.OK
+    x_dev = torch.from_numpy(x0).cuda()
+    B0_dev = torch.from_numpy(B0).cuda()
+    E_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert _energy_static(L, g, x_dev, B0_dev, E_dev) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        E_dev.fill_(float("nan"))
+        assert _energy_static(L, g, x_dev, B0_dev, E_dev) == 0
+        torch.cuda.synchronize()
+        assert abs(float(E_dev.item()) - E_ref) < 1e-13 * E_ref
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_energy_static_rejects_oversize_and_bad_args(L):
