@@ -6,7 +6,10 @@ mixed precision, two passes per stage in FP64 -- the fifth-order update
 with its embedded error, and the step control) over the 64^3 braid
 workload (6 twist regions, pre-distorted grid, FP64, mimetic current),
 timed whole with CUDA events, L2 flushed between steps.  Metric: interior
-node-stage updates per second (6 per interior node per attempt).
+node-stage updates per second (6 per interior node per attempt).  The block
+of K timed attempts is repeated until at least a second of device time has
+been timed (so that the clock sampler sees the load); `value` and
+`ms_per_step` are the mean over every timed attempt.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -17,6 +20,8 @@ workload (replicas; the step has no cross-GPU exchange in this build) and
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import math
 import os
@@ -44,14 +49,34 @@ ALGO_BYTES = {"fp64": 132.0, "mixed": 66.0}
 ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0}
 FP64_PEAK_FLOPS = 1.25e12      # nominal dense FP64 rate of GB300 (152 SMs)
 L2_FLUSH_BYTES = 512 << 20
+MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # DRAM bytes per stage from ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # of one attempt's six stages, averaged; FP64: both passes of a stage), keyed
-# by (n, precision, curl); absent workloads report null
+# by (n, precision, curl), with the hash of the kernel sources they were
+# captured from (kernel_source_hash()); a workload without an entry, or one
+# whose kernels have changed since, reports null
 NCU_TRAFFIC = {
-    (64, "fp64", "mimetic"): 45.89e6,
-    (64, "mixed", "mimetic"): 15.71e6,
-    (128, "mixed", "mimetic"): 155.34e6,
 }
+
+
+def kernel_source_hash():
+    """First 12 hex digits of the SHA-256 of the CUDA sources (sorted by
+    name): the traffic figures above are valid only for the kernels they
+    were measured on."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1405_0942_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(n, precision, curl):
+    ent = NCU_TRAFFIC.get((n, precision, curl))
+    if ent is None or ent[1] != kernel_source_hash():
+        return None
+    return ent[0]
 
 
 def load_peaks():
@@ -226,13 +251,14 @@ def reference_arm(args):
 # ------------------------------------------------------------------ ours
 
 
-def time_mode(G, torch, w, precision, curl, steps, warmup, flush):
-    """CUDA-event times (ms) of `steps` attempts, each timed whole: the
-    target reset and the attempt's kernels, which run back to back as
-    programmatic dependents.  Then the per-kernel split (ms, launch order:
-    six stages and the step control) of `steps` more attempts with an event
-    between stages; those events keep each stage from starting early, so the
-    split adds up to a little more than the whole attempt."""
+def time_mode(G, torch, w, precision, curl, steps, warmup, flush, min_s=MIN_TIMED_S):
+    """CUDA-event times (ms) of blocks of `steps` attempts, each attempt
+    timed whole (the target reset and the attempt's kernels, which run back
+    to back as programmatic dependents), the block repeated until `min_s`
+    seconds of device time have been timed.  Then the per-kernel split (ms,
+    launch order: six stages and the step control) of `steps` more attempts
+    with an event between stages; those events keep each stage from starting
+    early, so the split adds up to a little more than the whole attempt."""
     r = G.Relaxation(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.lo, w.grid.hi,
                      precision=G.MIXED if precision == "mixed" else G.FP64,
                      curl=G.DIRECT if curl == "direct" else G.MIMETIC)
@@ -241,21 +267,53 @@ def time_mode(G, torch, w, precision, curl, steps, warmup, flush):
     for _ in range(warmup):
         flush.zero_()
         r.attempts(1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for a, b in ev:
-        flush.zero_()                 # L2 flush, outside the event interval
-        a.record()
-        r.attempts(1)
-        b.record()
-    torch.cuda.synchronize()
-    whole = np.array([a.elapsed_time(b) for a, b in ev])
+    times = []
+    while True:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()                 # L2 flush, outside the event interval
+            a.record()
+            r.attempts(1)
+            b.record()
+        torch.cuda.synchronize()
+        times.extend(a.elapsed_time(b) for a, b in ev)
+        if sum(times) * 1e-3 >= min_s:
+            break
+    whole = np.array(times)
     split = []
     for _ in range(steps):
         flush.zero_()
         split.append(r.profile_attempt())
     st = r.stats()
     return r, whole, np.array(split), st
+
+
+FP64_CONTEXT = {}
+
+
+def fp64_context(torch):
+    """Beside the nominal FP64 rate: the SM count of this device and the rate
+    cuBLAS's FP64 GEMM reaches on it (4096^3, best of 3 after a warm-up),
+    a measured FP64 ceiling for context."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    n = 4096
+    a = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    b = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    FP64_CONTEXT.update(sm_count=props.multi_processor_count,
+                        dgemm_tflops=2.0 * n ** 3 / (best * 1e-3) / 1e12)
 
 
 def roofline_entry(whole, split, w, precision, curl, hbm_peak, peak_kind):
@@ -267,7 +325,7 @@ def roofline_entry(whole, split, w, precision, curl, hbm_peak, peak_kind):
     I = w.grid.n_interior
     bytes_per_attempt = ALGO_BYTES[precision] * I * 6
     gbs = bytes_per_attempt / (att_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get((w.grid.nx, precision, curl))
+    traffic = ncu_traffic(w.grid.nx, precision, curl)
     shares = (split[:, :6].mean(axis=0) / split.sum(axis=1).mean()).round(4).tolist()
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
            "frac": gbs / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -279,6 +337,8 @@ def roofline_entry(whole, split, w, precision, curl, hbm_peak, peak_kind):
         alu = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_FLOPS / 1e12,
                "unit": "TFLOP/s", "frac": fl * 1e12 / FP64_PEAK_FLOPS, "traffic": traffic,
                "peak_kind": "nominal FP64 rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+               "sm_count": FP64_CONTEXT.get("sm_count"),
+               "fp64_dgemm_tflops": FP64_CONTEXT.get("dgemm_tflops"),
                "algorithmic_flops_per_launch": ALGO_FLOPS_F64[curl] * I,
                "duration_basis": hbm["duration_basis"], "stage_shares": shares,
                "hbm_frac": hbm["frac"], "hbm_achieved_gbs": gbs}
@@ -380,14 +440,16 @@ def our_arm(args):
         if ws > 1:
             torch.distributed.barrier()
 
+    if args.precision == "fp64":
+        fp64_context(torch)
     barrier()
     sampler.start()
     r, whole, split, st = time_mode(G, torch, w, args.precision, args.curl, args.steps,
                                     args.warmup, flush)
     barrier()
     clocks = sampler.stop()
-    # device time of the K timed steps; slowest rank, units of all ranks
-    total_s, units = reduce_over_ranks(whole.sum() * 1e-3, w.grid.n_interior * 6 * args.steps,
+    # device time of every timed attempt; slowest rank, units of all ranks
+    total_s, units = reduce_over_ranks(whole.sum() * 1e-3, w.grid.n_interior * 6 * len(whole),
                                        ws, "cuda")
     value = units / total_s
     roof = roofline_entry(whole, split, w, args.precision, args.curl, hbm_peak, peak_kind)
@@ -400,7 +462,7 @@ def our_arm(args):
                 continue
             _, ms2, sp2, st2 = time_mode(G, torch, w, prec, curl, args.steps, args.warmup,
                                          flush)
-            v2 = w.grid.n_interior * 6 * args.steps / (ms2.sum() * 1e-3)
+            v2 = w.grid.n_interior * 6 / (ms2.mean() * 1e-3)
             extra[f"{prec}_{curl}"] = {
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.mean(),
                 "speedup_vs_primary": v2 / value,
@@ -408,16 +470,20 @@ def our_arm(args):
         if args.workload == "braid64":
             # the mixed-precision path where HBM, not L2, holds the fields:
             # the 128^3 braid of 10 twist regions (mixed-precision workload)
-            w128 = workload("braid128")
-            _, ms3, sp3, _ = time_mode(G, torch, w128, "mixed", "mimetic", args.steps,
-                                       args.warmup,
-                                  flush)
-            v3 = w128.grid.n_interior * 6 * args.steps / (ms3.sum() * 1e-3)
-            extra["mixed_mimetic_braid128"] = {
-                "value": v3, "unit": UNIT, "ms_per_step": ms3.mean(),
-                "workload": "braid128", "grid": [128, 128, 128],
-                "roofline": roofline_entry(ms3, sp3, w128, "mixed", "mimetic", hbm_peak,
-                                           peak_kind)}
+            # and the 384^3 production workload (12 regions + ABC, ~8 GB)
+            for name in ("braid128", "prod384"):
+                wl = workload(name)
+                r3, ms3, sp3, _ = time_mode(G, torch, wl, "mixed", "mimetic", args.steps,
+                                            args.warmup, flush)
+                v3 = wl.grid.n_interior * 6 / (ms3.mean() * 1e-3)
+                extra[f"mixed_mimetic_{name}"] = {
+                    "value": v3, "unit": UNIT, "ms_per_step": ms3.mean(),
+                    "timed_attempts": len(ms3), "workload": name,
+                    "grid": [wl.grid.nx, wl.grid.ny, wl.grid.nz],
+                    "roofline": roofline_entry(ms3, sp3, wl, "mixed", "mimetic", hbm_peak,
+                                               peak_kind)}
+                del r3, wl
+                torch.cuda.empty_cache()
     e2e = None
     if not args.lean:
         # every rank drives its own replica through the C ABI with host
@@ -444,13 +510,15 @@ def our_arm(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": whole.mean(),
+        "timed_attempts": len(whole), "repeats": len(whole) // args.steps,
+        "timed_s": float(whole.sum() * 1e-3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded braid field and pre-distorted grid)",
         "config": config_dict(args, w), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
         "clocks": clocks,
         # per timed attempt: the target reset plus the attempt's kernels
-        "gpu_launches": (r.kernels_per_attempt() + 1) * args.steps,
+        "gpu_launches": (r.kernels_per_attempt() + 1) * len(whole),
         "kernel_ms": {"stages": per_kernel[:6], "control": per_kernel[6]},
         "attempts": {"accepted": st["accepted"], "rejected": st["rejected"]},
         "compare": extra,

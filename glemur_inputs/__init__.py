@@ -152,6 +152,19 @@ def isohelix_field(X, B0=1.0, a_r=math.sqrt(2.0), a_z=2.0, phi=math.pi / 4):
     return np.stack([f * y, -f * x, np.full_like(x, B0)])
 
 
+def isohelix_relaxed(X, B0=1.0, a_r=math.sqrt(2.0), a_z=2.0, phi=math.pi / 4):
+    """The IsoHelix field's exact relaxed state (eqs. "B relaxed" and "x
+    analytical relaxed"): positions x_relax -- each plane Z = const turned
+    about the z axis by the angle phi exp(-(X^2+Y^2)/a_r^2 - Z^2/a_z^2) --
+    and the field B_relax = B0 e_z, both sampled on the nodes."""
+    x, y, z = X
+    th = phi * np.exp(-(x * x + y * y) / a_r ** 2 - z * z / a_z ** 2)
+    c, s = np.cos(th), np.sin(th)
+    xr = np.stack([c * x + s * y, c * y - s * x, z.copy()])
+    Br = np.stack([np.zeros_like(x), np.zeros_like(x), np.full_like(x, B0)])
+    return xr, Br
+
+
 # ---------------------------------------------------------------- grids
 
 

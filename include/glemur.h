@@ -240,6 +240,37 @@ int glemur_forcefree_err(glemur_ctx* ctx, double* xi, double* xi_sin);
  * ring (first < accepted - GLEMUR_DT_LOG).  Synchronises. */
 int glemur_get_dt_schedule(glemur_ctx* ctx, long long first, int count, double* dts);
 
+/* ---- validation diagnostics (section "Diagnostics") --------------------
+ * On the current accepted state, FP64 arithmetic in either precision,
+ * deterministic sums; each synchronises the stream. */
+
+/* Section "Deviation from the Exact Known Equilibrium": *sigma_x and
+ * *sigma_B, the root mean square over all N nodes of |x - x_ref| and of
+ * |B - B_ref| (B the pull-back of eq. "B transformation").  x_ref and B_ref
+ * are device float64 fields (layout above), e.g. the IsoHelix field's
+ * closed-form relaxed state (eqs. "x analytical relaxed", "B relaxed").
+ * Errors: BADARG, CUDA. */
+int glemur_deviation(glemur_ctx* ctx, const double* x_ref, const double* B_ref,
+                     double* sigma_x, double* sigma_B);
+
+/* Section "Force-Freeness": alpha* = J.B / B^2 at the nodes (i, j, k) of the
+ * node line through (i, j) (1 <= i <= nx-2, 1 <= j <= ny-2), with the
+ * context's current, into host alpha[nz] when non-NULL (the two boundary
+ * entries, where the current is not defined, are NaN), and eq. "epsilon
+ * star": *eps_star = max over pairs of its interior nodes of
+ * a_r (alpha*_k - alpha*_l) / |X_k - X_l| (a_r > 0; |X_k - X_l| =
+ * |k - l| h_z).  nz <= 6144.  Errors: BADARG, CUDA. */
+int glemur_alpha_line(glemur_ctx* ctx, int i, int j, double a_r, double* alpha,
+                      double* eps_star);
+
+/* Section "Convexity", eq. "convexity": kappa = +1 at a node when each
+ * trihedron of its index neighbours x(i+di,j,k) - x, x(i,j+dj,k) - x,
+ * x(i,j,k+dk) - x (di, dj, dk = +-1, the neighbours inside the grid) has a
+ * determinant of sign di dj dk, else -1.  *n_concave receives the number of
+ * nodes with kappa = -1; kappa (device, N int8 values) may be NULL.
+ * Errors: BADARG, CUDA. */
+int glemur_convexity(glemur_ctx* ctx, long long* n_concave, signed char* kappa);
+
 /* Counters and last-attempt values (see glemur_stats).  Synchronises. */
 int glemur_get_stats(glemur_ctx* ctx, glemur_stats* stats);
 

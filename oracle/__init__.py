@@ -88,6 +88,10 @@ def lib():
         L.ora_step_fixed.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, C.c_double, _dp]
         L.ora_energy.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
         L.ora_forcefree.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, _dp, _dp]
+        L.ora_deviation.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, _dp, _dp]
+        L.ora_alpha_line.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, C.c_int, C.c_int,
+                                     C.c_double, _dp, _dp]
+        L.ora_convexity.argtypes = [C.POINTER(_Grid), _dp, C.c_void_p, C.POINTER(C.c_long)]
         L.orc_velocity.argtypes = [C.POINTER(_Grid), C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_relax_loss.argtypes = [C.POINTER(_Grid), C.c_void_p, C.c_void_p, _dp, C.c_int,
                                      C.c_int, C.c_void_p]
@@ -240,6 +244,35 @@ def forcefree(grid, x, B0, curl=MIMETIC):
     a, b = np.zeros(1), np.zeros(1)
     rc = lib().ora_forcefree(C.byref(_g(grid)), curl, _p(x), _p(B0), _p(a), _p(b))
     return float(a[0]), float(b[0]), rc
+
+
+def deviation(grid, x, B0, x_ref, B_ref):
+    """(sigma_x, sigma_B, rc): RMS over nodes of |x - x_ref| and |B - B_ref|."""
+    x, B0, x_ref, B_ref = _f(x), _f(B0), _f(x_ref), _f(B_ref)
+    a, b = np.zeros(1), np.zeros(1)
+    rc = lib().ora_deviation(C.byref(_g(grid)), _p(x), _p(B0), _p(x_ref), _p(B_ref),
+                             _p(a), _p(b))
+    return float(a[0]), float(b[0]), rc
+
+
+def alpha_line(grid, x, B0, i, j, a_r, curl=MIMETIC):
+    """(alpha* along the node line (i, j, .) -- NaN at its two boundary
+    nodes --, epsilon*, rc)."""
+    x, B0 = _f(x), _f(B0)
+    alpha = np.zeros(grid.nz)
+    e = np.zeros(1)
+    rc = lib().ora_alpha_line(C.byref(_g(grid)), curl, _p(x), _p(B0), i, j, a_r,
+                              _p(alpha), _p(e))
+    return alpha, float(e[0]), rc
+
+
+def convexity(grid, x):
+    """(kappa per node as int32 (nz, ny, nx), number of concave nodes)."""
+    x = _f(x)
+    kappa = np.zeros((grid.nz, grid.ny, grid.nx), dtype=np.int32)
+    n = C.c_long(0)
+    lib().ora_convexity(C.byref(_g(grid)), _p(x), kappa.ctypes.data, C.byref(n))
+    return kappa, int(n.value)
 
 
 # ---------------------------------------------------------------- complex step

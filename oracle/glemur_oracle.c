@@ -766,3 +766,110 @@ int ora_forcefree(const ora_grid* g, int curl, const double* x,
   free(J);
   return rc;
 }
+
+/* ------------------------------------------- validation diagnostics */
+
+/* Section "Deviation from the Exact Known Equilibrium": sigma_x and sigma_B,
+ * root-mean-square over all N nodes of |x - x_ref| and |B - B_ref|. */
+int ora_deviation(const ora_grid* g, const double* x, const double* B0,
+                  const double* x_ref, const double* B_ref, double* sigma_x,
+                  double* sigma_B) {
+  long N = n_nodes(g);
+  double* B = (double*)malloc(sizeof(double) * 3 * N);
+  if (!B) return ORA_ERR_BADARG;
+  int rc = ora_pullback(g, x, B0, B, NULL);
+  double sx = 0.0, sb = 0.0;
+  for (long n = 0; n < N; ++n)
+    for (int c = 0; c < 3; ++c) {
+      double dx = x[c * N + n] - x_ref[c * N + n];
+      double db = B[c * N + n] - B_ref[c * N + n];
+      sx += dx * dx;
+      sb += db * db;
+    }
+  *sigma_x = sqrt(sx / (double)N);
+  *sigma_B = sqrt(sb / (double)N);
+  free(B);
+  return rc;
+}
+
+/* Section "Force-Freeness": alpha* = J.B / B^2 at the interior nodes
+ * (i, j, k), k = 1 .. nz-2, of the node line through (i, j) (alpha[k]; the
+ * two boundary entries, where the current is not defined, are NaN), and
+ * eq. "epsilon star": the largest a_r (alpha*_k - alpha*_l) / |X_k - X_l|
+ * over pairs of those nodes, |X_k - X_l| = |k - l| h_z on the line. */
+int ora_alpha_line(const ora_grid* g, int curl, const double* x,
+                   const double* B0, int i, int j, double a_r, double* alpha,
+                   double* eps_star) {
+  if (i < 1 || i > g->nx - 2 || j < 1 || j > g->ny - 2) return ORA_ERR_BADARG;
+  long N = n_nodes(g);
+  double* B = (double*)malloc(sizeof(double) * 3 * N);
+  double* J = (double*)malloc(sizeof(double) * 3 * N);
+  if (!B || !J) {
+    free(B);
+    free(J);
+    return ORA_ERR_BADARG;
+  }
+  int rc = ora_pullback(g, x, B0, B, NULL);
+  int rc2 = curl == ORA_CURL_DIRECT ? ora_curl_direct(g, x, B0, J)
+                                    : ora_curl_mimetic(g, x, B, J, NULL);
+  if (rc == ORA_OK) rc = rc2;
+  alpha[0] = alpha[g->nz - 1] = NAN;
+  for (int k = 1; k < g->nz - 1; ++k) {
+    double Jn[3], Bn[3];
+    get3(g, J, i, j, k, Jn);
+    get3(g, B, i, j, k, Bn);
+    alpha[k] = dot(Jn, Bn) / dot(Bn, Bn);
+  }
+  double e = 0.0;
+  for (int k = 1; k < g->nz - 1; ++k)
+    for (int l = 1; l < g->nz - 1; ++l) {
+      if (l == k) continue;
+      double v = a_r * (alpha[k] - alpha[l]) / (fabs((double)(k - l)) * g->h[2]);
+      if (!(v <= e)) e = v;
+    }
+  *eps_star = e;
+  free(B);
+  free(J);
+  return rc;
+}
+
+/* Section "Convexity", eq. "convexity": at node (i, j, k) the trihedra of
+ * dx^lambda = x(i+di, j, k) - x, dx^mu = x(i, j+dj, k) - x and
+ * dx^nu = x(i, j, k+dk) - x for the eight sign choices (di, dj, dk); the
+ * node is convex (kappa = +1) when the determinant of every trihedron whose
+ * three neighbours exist has the sign di dj dk, else kappa = -1.  kappa
+ * (N ints) may be NULL; *n_concave counts the nodes with kappa = -1. */
+int ora_convexity(const ora_grid* g, const double* x, int* kappa,
+                  long* n_concave) {
+  long cnt = 0;
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) {
+        double xc[3];
+        get3(g, x, i, j, k, xc);
+        int ok = 1;
+        for (int di = -1; di <= 1; di += 2)
+          for (int dj = -1; dj <= 1; dj += 2)
+            for (int dk = -1; dk <= 1; dk += 2) {
+              if (i + di < 0 || i + di >= g->nx || j + dj < 0 || j + dj >= g->ny ||
+                  k + dk < 0 || k + dk >= g->nz)
+                continue;
+              double a[3], b[3], c[3], F[9];
+              get3(g, x, i + di, j, k, a);
+              get3(g, x, i, j + dj, k, b);
+              get3(g, x, i, j, k + dk, c);
+              for (int r = 0; r < 3; ++r) {
+                F[r * 3 + 0] = a[r] - xc[r];
+                F[r * 3 + 1] = b[r] - xc[r];
+                F[r * 3 + 2] = c[r] - xc[r];
+              }
+              double D = det3(F);
+              int sgn = D > 0.0 ? 1 : (D < 0.0 ? -1 : 0);
+              if (sgn != di * dj * dk) ok = 0;
+            }
+        if (kappa) kappa[node(g, i, j, k)] = ok ? 1 : -1;
+        if (!ok) ++cnt;
+      }
+  *n_concave = cnt;
+  return ORA_OK;
+}

@@ -153,6 +153,29 @@ int ora_energy(const ora_grid* g, const double* x, const double* B0,
 int ora_forcefree(const ora_grid* g, int curl, const double* x,
                   const double* B0, double* xi, double* xi_sin);
 
+/* --- validation diagnostics (section "Diagnostics") ---------------------- */
+
+/* Section "Deviation from the Exact Known Equilibrium": sigma_x and sigma_B,
+ * the root mean square over all N nodes of |x - x_ref| and |B - B_ref|
+ * (B the pull-back of B0 on x). */
+int ora_deviation(const ora_grid* g, const double* x, const double* B0,
+                  const double* x_ref, const double* B_ref, double* sigma_x,
+                  double* sigma_B);
+
+/* Section "Force-Freeness": alpha* = J.B/B^2 along the node line (i, j, k),
+ * k = 1 .. nz-2 (alpha has nz entries, the boundary ones NaN), and
+ * epsilon* = max over pairs of a_r (alpha_k - alpha_l) / |X_k - X_l|. */
+int ora_alpha_line(const ora_grid* g, int curl, const double* x,
+                   const double* B0, int i, int j, double a_r, double* alpha,
+                   double* eps_star);
+
+/* Section "Convexity", eq. "convexity": kappa = +1 at a node when every
+ * trihedron of its index neighbours (di, dj, dk = +-1, neighbours inside
+ * the grid) has a determinant of sign di dj dk, else -1; *n_concave counts
+ * the -1 nodes (kappa may be NULL). */
+int ora_convexity(const ora_grid* g, const double* x, int* kappa,
+                  long* n_concave);
+
 #ifdef __cplusplus
 }
 #endif

@@ -362,6 +362,7 @@ struct glemur_ctx {
   void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
   double* rb;                            // split path: 1/det G
+  double* Gb;                            // split path: g_0, g_1, g_2
   int max_blocks, nblocks, kz;          // mimetic-current launches
   int split_grid_b[6] = {}, split_grid_c[6] = {};  // FP64 two-pass grids (CTAs)
   int nblocks_direct, kz_direct;         // direct-current launches
@@ -398,7 +399,8 @@ Layout layout(int nx, int ny, int nz, int precision) {
   // two stage inputs (mimetic stages); FP64 also B and 1/det G for the
   // two-pass stages
   L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
-                                                          align256((size_t)N * 8)
+                                                          align256((size_t)N * 8) +
+                                                          align256((size_t)(9 * N) * 8)
                                                     : 0);
   L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.split;
   return L;
@@ -495,6 +497,7 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.ys[1] = (double*)c->ys[1];
   a.Bb = c->Bb;
   a.rb = c->rb;
+  a.Gb = c->Gb;
   a.diag = diag;
   a.force = force;
   a.st = c->st;
@@ -721,6 +724,7 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
     if (s < 5) a.ys[(s + 1) & 1] = yS[s + 1];
     a.Bb = BS[s];
     a.rb = RS[s];
+    a.Gb = c->Gb;
     a.diag = 0;
     a.force = 1;
     a.st = c->st;
@@ -751,6 +755,26 @@ int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precisi
   *B0s = c->B0s;
   for (int j = 0; j < 5; ++j) k[j] = c->k[j];
   *stream = (void*)c->s;
+  return GLEMUR_OK;
+}
+
+int ctx_diag(glemur_ctx* c, DiagCtx* o) {
+  o->nx = c->nx;
+  o->ny = c->ny;
+  o->nz = c->nz;
+  for (int a = 0; a < 3; ++a) {
+    o->lo[a] = c->lo[a];
+    o->h[a] = c->h[a];
+  }
+  o->precision = c->o.precision;
+  o->curl = c->o.curl;
+  o->dbuf_dev = (const void* const*)c->dbuf_dev;
+  o->B0s = c->B0s;
+  o->st = c->st;
+  o->part = c->part;
+  o->max_blocks = c->max_blocks;
+  o->stage = c->stage;
+  o->s = c->s;
   return GLEMUR_OK;
 }
 
@@ -827,12 +851,13 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->dtlog = (double*)p; p += L.dtlog;
   c->max_blocks = L.max_blocks;
   c->split = 0;
-  c->ys[0] = c->ys[1] = c->Bb = c->rb = nullptr;
+  c->ys[0] = c->ys[1] = c->Bb = c->rb = c->Gb = nullptr;
   c->ys[0] = p; p += L.field;
   c->ys[1] = p; p += L.field;
   if (o.precision == GLEMUR_FP64) {
     c->Bb = (double*)p; p += align256((size_t)(3 * c->N) * 8);
-    c->rb = (double*)p;
+    c->rb = (double*)p; p += align256((size_t)c->N * 8);
+    c->Gb = (double*)p;
     const char* fused = getenv("GLEMUR_F64_FUSED");
     c->split = !(fused && atoi(fused) > 0);
   }

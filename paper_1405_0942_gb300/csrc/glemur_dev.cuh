@@ -158,12 +158,29 @@ struct SplitArgs {
                        // boundary entries hold the fixed boundary positions
   double* Bb;          // B, 3N
   double* rb;          // 1/det G, N
+  double* Gb;          // index-space differences g_0, g_1, g_2 at every
+                       // interior node, 9N: component c of g_a at
+                       // Gb[(3a + c) N + n] (written by pass B, read by C)
   int diag, force;
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;         // partial stride: the largest of the grids
   int grid_b[6];       // CTAs of pass B of each stage
   int grid_c[6];       // CTAs of pass C of each stage
+};
+
+// What the on-demand diagnostics (diagnostics.cu) need of a context.
+struct DiagCtx {
+  int nx, ny, nz;
+  double lo[3], h[3];
+  int precision, curl;
+  const void* const* dbuf_dev;  // device copy of the two displacement buffers
+  const void* B0s;              // pre-scaled B0 in storage precision
+  const DevState* st;           // .cur selects the accepted displacement
+  double* part;                 // NPART * max_blocks doubles of scratch
+  int max_blocks;
+  double* stage;                // 3N doubles of scratch
+  cudaStream_t s;
 };
 
 __device__ __forceinline__ long long nidx(int i, int j, int k, int nx, int ny) {

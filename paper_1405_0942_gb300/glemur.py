@@ -56,7 +56,8 @@ EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
            "glemur_profile_attempt", "glemur_energy_static", "glemur_destroy",
            "glemur_strerror", "glemur_adjoint_workspace_bytes", "glemur_vjp_step",
            "glemur_loss_grad", "glemur_param_contract", "glemur_state_bytes",
-           "glemur_get_state", "glemur_set_state", "glemur_get_dt_schedule"]
+           "glemur_get_state", "glemur_set_state", "glemur_get_dt_schedule",
+           "glemur_deviation", "glemur_alpha_line", "glemur_convexity"]
 DT_LOG = 65536  # accepted step sizes the device keeps (GLEMUR_DT_LOG)
 LOSS_ENERGY, LOSS_XI = 0, 1
 
@@ -97,6 +98,9 @@ def lib() -> C.CDLL:
     L.glemur_forcefree_err.argtypes = [vp, dp, dp]
     L.glemur_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.glemur_get_dt_schedule.argtypes = [vp, C.c_longlong, ip, dp]
+    L.glemur_deviation.argtypes = [vp, vp, vp, dp, dp]
+    L.glemur_alpha_line.argtypes = [vp, ip, ip, C.c_double, dp, dp]
+    L.glemur_convexity.argtypes = [vp, C.POINTER(C.c_longlong), vp]
     L.glemur_kernels_per_attempt.argtypes = [vp]
     L.glemur_profile_attempt.argtypes = [vp, C.POINTER(C.c_float), ip]
     L.glemur_energy_static.argtypes = [ip, ip, ip, dp, dp, vp, vp, vp, vp]
@@ -288,6 +292,43 @@ class Relaxation:
         _check(lib().glemur_forcefree_err(self._h, C.byref(a), C.byref(b)),
                "glemur_forcefree_err")
         return a.value, b.value
+
+    def deviation(self, x_ref, B_ref):
+        """(sigma_x, sigma_B) of the current state against the CUDA float64
+        fields x_ref, B_ref (e.g. a closed-form relaxed state)."""
+        for t in (x_ref, B_ref):
+            p, mem, _ = _field_ptr(t, self.shape)
+            if mem != MEM_DEVICE:
+                raise ValueError("deviation() takes CUDA float64 fields")
+        a, b = C.c_double(), C.c_double()
+        _check(lib().glemur_deviation(self._h, C.c_void_p(x_ref.data_ptr()),
+                                      C.c_void_p(B_ref.data_ptr()), C.byref(a), C.byref(b)),
+               "glemur_deviation")
+        return a.value, b.value
+
+    def alpha_line(self, i, j, a_r):
+        """(alpha* along the node line (i, j, .) as a numpy array -- NaN at
+        its two boundary nodes --, epsilon*)."""
+        alpha = np.empty(self.dims[2], dtype=np.float64)
+        e = C.c_double()
+        _check(lib().glemur_alpha_line(self._h, int(i), int(j), float(a_r),
+                                       alpha.ctypes.data_as(C.POINTER(C.c_double)),
+                                       C.byref(e)), "glemur_alpha_line")
+        return alpha, e.value
+
+    def convexity(self, with_field=False):
+        """Number of concave nodes (kappa = -1); with_field=True also returns
+        kappa as an int8 CUDA tensor of shape (nz, ny, nx)."""
+        import torch
+        n = C.c_longlong()
+        kap = None
+        if with_field:
+            nx, ny, nz = self.dims
+            kap = torch.empty((nz, ny, nx), dtype=torch.int8, device=self.device)
+        _check(lib().glemur_convexity(self._h, C.byref(n),
+                                      C.c_void_p(kap.data_ptr() if kap is not None else 0)),
+               "glemur_convexity")
+        return (n.value, kap) if with_field else n.value
 
     def kernels_per_attempt(self):
         return int(lib().glemur_kernels_per_attempt(self._h))

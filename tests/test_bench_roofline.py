@@ -28,7 +28,9 @@ def test_mixed_roofline_is_bytes_over_whole_attempt():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert np.isclose(r["achieved"], gbs) and np.isclose(r["frac"], gbs / 6783.8)
     assert r["algorithmic_bytes_per_launch"] == 66.0 * I
-    assert r["traffic"] == bench.NCU_TRAFFIC[(128, "mixed", "mimetic")]
+    ent = bench.NCU_TRAFFIC.get((128, "mixed", "mimetic"))
+    fresh = ent is not None and ent[1] == bench.kernel_source_hash()
+    assert r["traffic"] == (ent[0] if fresh else None)
     assert np.isclose(sum(r["stage_shares"]), 0.36 / 0.37, atol=1e-3)
 
 
@@ -49,3 +51,14 @@ def test_workload_without_a_capture_reports_null_traffic():
     r = bench.roofline_entry(np.array([1.0]), np.array([[0.1] * 7]), _W(96), "mixed",
                              "direct", 6783.8, "measured")
     assert r["traffic"] is None
+
+
+def test_traffic_goes_null_when_the_kernels_change(monkeypatch):
+    """A traffic figure is reported only with the kernel sources it was
+    captured on: an entry carrying another source hash reads as null."""
+    h = bench.kernel_source_hash()
+    assert len(h) == 12
+    monkeypatch.setitem(bench.NCU_TRAFFIC, (40, "mixed", "mimetic"), (1.5e6, h))
+    monkeypatch.setitem(bench.NCU_TRAFFIC, (41, "mixed", "mimetic"), (1.5e6, "0" * 12))
+    assert bench.ncu_traffic(40, "mixed", "mimetic") == 1.5e6
+    assert bench.ncu_traffic(41, "mixed", "mimetic") is None
