@@ -74,6 +74,9 @@ class Grid:
     nz: int
     lo: tuple = (-1.0, -1.0, -1.0)
     hi: tuple = (1.0, 1.0, 1.0)
+    # periodic in z: planes 0 and nz-1 are ghosts of planes nz-2 and 1,
+    # shifted by the period (nz - 2) h_z (section "Boundary Conditions")
+    periodic_z: bool = False
 
     @property
     def shape(self):
@@ -300,3 +303,38 @@ WORKLOADS = {
     "adjoint96": ("adjoint", 96, "96^3 6-region braid, FP64 adjoint over 500 steps"),
     "prod384": ("prod", 384, "384^3 12-region braid + 0.1 ABC, mixed precision"),
 }
+
+
+# ---------------------------------------------------------------- periodic
+
+
+def periodic_fields(X, P, seed=6, amp=0.05):
+    """Positions and field that repeat along z with period P, sampled at the
+    labels X: two twist regions modulated by sin(2 pi Z / P + phase) and
+    cos(4 pi Z / P + phase) (divergence-free for any z profile) on e_z, and
+    the periodic pre-distortion x_a = X_a + amp sin(pi X_a + phi_a)
+    (a = x, y; the x and y faces stay planar), z = Z + amp sin(2 pi Z / P +
+    phi_z).  Returns (x0, B0)."""
+    rng = SplitMix64(seed)
+    ph = [2.0 * math.pi * rng.uniform() for _ in range(5)]
+    x, y, z = X
+    w = 2.0 * math.pi / P
+    G1 = np.exp(-(x * x + y * y) / 0.25) * np.sin(w * z + ph[3])
+    dx2, dy2 = x - 0.3, y + 0.2
+    G2 = -0.8 * np.exp(-(dx2 * dx2 + dy2 * dy2) / 0.16) * np.cos(2.0 * w * z + ph[4])
+    B0 = np.stack([-y * G1 - dy2 * G2, x * G1 + dx2 * G2, np.ones_like(z)])
+    x0 = np.stack([x + amp * np.sin(math.pi * x + ph[0]),
+                   y + amp * np.sin(math.pi * y + ph[1]),
+                   z + amp * np.sin(w * z + ph[2])])
+    return x0, B0
+
+
+def periodic_case(nx, ny, m, seed=6, lo_z=-1.0, h_z=2.0 / 31.0):
+    """A z-periodic workload of m inner planes (period P = m h_z): the grid
+    (nz = m + 2, ghost planes 0 and m+1 included) and x0, B0 of
+    :func:`periodic_fields`, whose ghost nodes sit one period from their
+    partners.  Returns (grid, x0, B0)."""
+    g = Grid(nx, ny, m + 2, lo=(-1.0, -1.0, lo_z), hi=(1.0, 1.0, lo_z + (m + 1) * h_z),
+             periodic_z=True)
+    x0, B0 = periodic_fields(nodes(g), m * g.h[2], seed)
+    return g, x0, B0

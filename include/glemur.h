@@ -59,7 +59,13 @@ enum glemur_precision {
 
 enum glemur_curl {
   GLEMUR_CURL_MIMETIC = 0, /* nearest-neighbour Stokes loops (default) */
-  GLEMUR_CURL_DIRECT = 1   /* direct derivatives of B = F B0 / det F */
+  GLEMUR_CURL_DIRECT = 1,  /* direct derivatives of B = F B0 / det F */
+  GLEMUR_CURL_NNN = 2      /* next-nearest-neighbour (octilateral) loops of
+                              section "Next Nearest Neighbor Mimetic
+                              Approach", eqs. "eight surfaces" and "sum of
+                              eight triangles"; GLEMUR_FP64 only, no adjoint.
+                              The paper finds it unstable in all but one of
+                              its runs. */
 };
 
 enum glemur_mem { GLEMUR_MEM_DEVICE = 0, GLEMUR_MEM_HOST = 1 };
@@ -100,6 +106,17 @@ typedef struct {
                          is the law as printed.  s < 1 (0.9 in Numerical
                          Recipes' stepper) ends rejection streaks when the
                          error falls more slowly than dt^5 */
+  int periodic_z;     /* 0 (default): every face line-tied.  1: periodic in
+                         z as in section "Boundary Conditions": node planes
+                         k = 0 and k = nz-1 are ghosts of the last and first
+                         inner planes (f = 1, l = nz-2) shifted by
+                         L_z + dZ = (nz - 2) h_z along z, so the period is
+                         the nz - 2 inner planes; glemur_set_x takes the
+                         ghost positions from their partners, glemur_energy
+                         sums one period.  The x and y faces stay
+                         line-tied; B0 must be periodic.  GLEMUR_FP64 with
+                         the nearest- or next-nearest-neighbour current;
+                         no adjoint. */
 } glemur_opts;
 
 typedef struct {

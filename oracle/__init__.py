@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-MIMETIC, DIRECT = 0, 1
+MIMETIC, DIRECT, NNN = 0, 1, 2
 OK, ERR_BADARG, ERR_COLLAPSED, ERR_NONFINITE, ERR_DT_UNDERFLOW = 0, -1, -3, -4, -5
 
 _dp = C.POINTER(C.c_double)
@@ -25,7 +25,7 @@ _dp = C.POINTER(C.c_double)
 
 class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("h", C.c_double * 3)]
+                ("h", C.c_double * 3), ("periodic_z", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -72,6 +72,7 @@ def lib():
         L.ora_mimetic_loops_at.argtypes = [C.POINTER(_Grid), _dp, _dp, C.c_int, C.c_int,
                                            C.c_int, _dp, _dp, _dp]
         L.ora_curl_direct.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
+        L.ora_curl_nnn.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
         L.ora_lorentz_velocity.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
         L.ora_lorentz_velocity.restype = None
         L.ora_velocity.argtypes = [C.POINTER(_Grid), C.c_int, _dp, _dp, _dp]
@@ -100,7 +101,8 @@ def lib():
 
 
 def _g(grid) -> _Grid:
-    return _Grid(grid.nx, grid.ny, grid.nz, (C.c_double * 3)(*grid.h))
+    return _Grid(grid.nx, grid.ny, grid.nz, (C.c_double * 3)(*grid.h),
+                 int(getattr(grid, "periodic_z", False)))
 
 
 def _p(a: np.ndarray):
@@ -151,6 +153,13 @@ def curl_direct(grid, x, B0):
     x, B0 = _f(x), _f(B0)
     J = _field(grid)
     rc = lib().ora_curl_direct(C.byref(_g(grid)), _p(x), _p(B0), _p(J))
+    return J, rc
+
+
+def curl_nnn(grid, x, B):
+    x, B = _f(x), _f(B)
+    J = _field(grid)
+    rc = lib().ora_curl_nnn(C.byref(_g(grid)), _p(x), _p(B), _p(J))
     return J, rc
 
 

@@ -48,6 +48,40 @@ static int is_interior(const ora_grid* g, int i, int j, int k) {
          k < g->nz - 1;
 }
 
+/* ------------------------------------------------- periodic boundaries */
+
+/* Section "Boundary Conditions", periodic in z: the ghost planes k = 0 and
+ * k = nz-1 repeat the last and first inner planes (f = 1, l = nz-2),
+ * shifted by L_z + dZ, where L_z = Z_l - Z_f is the extent of the inner
+ * planes and dZ the initial spacing: (nz - 3) h_z + h_z. */
+static double period_z(const ora_grid* g) {
+  return (double)(g->nz - 3) * g->h[2] + g->h[2];
+}
+
+static void refresh_ghosts(const ora_grid* g, double* x) {
+  if (!g->periodic_z) return;
+  long N = (long)g->nx * g->ny * g->nz;
+  double P = period_z(g);
+  for (int j = 0; j < g->ny; ++j)
+    for (int i = 0; i < g->nx; ++i) {
+      long f = ((long)1 * g->ny + j) * g->nx + i;
+      long l = ((long)(g->nz - 2) * g->ny + j) * g->nx + i;
+      long gf = ((long)0 * g->ny + j) * g->nx + i;
+      long gl = ((long)(g->nz - 1) * g->ny + j) * g->nx + i;
+      for (int c = 0; c < 3; ++c) {
+        x[c * N + gf] = x[c * N + l] - (c == 2 ? P : 0.0);
+        x[c * N + gl] = x[c * N + f] + (c == 2 ? P : 0.0);
+      }
+    }
+}
+
+/* The plane whose B a node's plane carries: ghosts carry their partner's
+ * (B(X_{f-1}) = B(X_l), B(X_{l+1}) = B(X_f)). */
+static int b_plane(const ora_grid* g, int k) {
+  if (!g->periodic_z) return k;
+  return k == 0 ? g->nz - 2 : (k == g->nz - 1 ? 1 : k);
+}
+
 /* ------------------------------------------------------------ 3-vectors */
 
 static void cross(const double a[3], const double b[3], double out[3]) {
@@ -167,7 +201,7 @@ int ora_pullback(const ora_grid* g, const double* x, const double* B0,
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
         double b[3], D;
-        if (pullback_at(g, x, B0, i, j, k, b, &D) != ORA_OK)
+        if (pullback_at(g, x, B0, i, j, b_plane(g, k), b, &D) != ORA_OK)
           rc = ORA_ERR_COLLAPSED;
         long n = node(g, i, j, k);
         B[n] = b[0];
@@ -294,6 +328,107 @@ int ora_curl_mimetic(const ora_grid* g, const double* x, const double* B,
         }
         if (mimetic_solve(xv, Bv, xc, c, M, Jn, area_gap) != ORA_OK)
           rc = ORA_ERR_COLLAPSED;
+        long n = node(g, i, j, k);
+        J[n] = Jn[0];
+        J[N + n] = Jn[1];
+        J[2 * N + n] = Jn[2];
+      }
+  return rc;
+}
+
+/* ---------------------------------------------------- next-nearest J */
+
+/* The octilateral of section "Next Nearest Neighbor Mimetic Approach" in
+ * surface r (spanned by index directions p = r+1, q = r+2 mod 3, as for the
+ * nearest-neighbour loops): the eight in-plane neighbours visited
+ * counter-clockwise about +r, starting at a corner,
+ *   V1 = +e_p - e_q, V2 = +e_p, V3 = +e_p + e_q, V4 = +e_q,
+ *   V5 = -e_p + e_q, V6 = -e_p, V7 = -e_p - e_q, V8 = -e_q,
+ * so that edges 2 and 3, 4 and 5, 6 and 7, 8 and 1 meet at the four
+ * corners, as the corner triangles of eq. "eight surfaces" need. */
+static void octilateral_vertices(int r, const int c[3], int v[8][3]) {
+  static const int off[8][2] = {{1, -1}, {1, 0},  {1, 1},   {0, 1},
+                                {-1, 1}, {-1, 0}, {-1, -1}, {0, -1}};
+  int p = (r + 1) % 3, q = (r + 2) % 3;
+  for (int m = 0; m < 8; ++m) {
+    v[m][0] = c[0];
+    v[m][1] = c[1];
+    v[m][2] = c[2];
+    v[m][p] += off[m][0];
+    v[m][q] += off[m][1];
+  }
+}
+
+/* Eq. "current discrete" over the octilateral (edge-mean B, eight
+ * contributions) and its vector area by eq. "sum of eight triangles": the
+ * four corner triangles dx_2 x dx_3 / 2, ..., dx_8 x dx_1 / 2 and the inner
+ * quadrilateral through V2, V4, V6, V8 with edges dx_A .. dx_D, whose area
+ * is (dx_A x dx_B + dx_B x dx_C + dx_C x dx_D + dx_D x dx_A) / 4. */
+static void octilateral_loop(const double xv[8][3], const double Bv[8][3],
+                             double* circ, double nA[3]) {
+  double dx[8][3];
+  *circ = 0.0;
+  for (int r = 0; r < 8; ++r) {
+    double Bm[3];
+    for (int a = 0; a < 3; ++a) {
+      dx[r][a] = xv[(r + 1) % 8][a] - xv[r][a];
+      Bm[a] = (Bv[r][a] + Bv[(r + 1) % 8][a]) / 2.0;
+    }
+    *circ += dot(Bm, dx[r]);
+  }
+  nA[0] = nA[1] = nA[2] = 0.0;
+  /* corner triangles: (dx_2, dx_3), (dx_4, dx_5), (dx_6, dx_7), (dx_8, dx_1) */
+  for (int t = 0; t < 4; ++t) {
+    double c[3];
+    cross(dx[2 * t + 1], dx[(2 * t + 2) % 8], c);
+    for (int a = 0; a < 3; ++a) nA[a] += c[a] / 2.0;
+  }
+  /* inner quadrilateral V2 -> V4 -> V6 -> V8 */
+  double q[4][3];
+  for (int a = 0; a < 3; ++a) {
+    q[0][a] = xv[3][a] - xv[1][a]; /* dx_A */
+    q[1][a] = xv[5][a] - xv[3][a]; /* dx_B */
+    q[2][a] = xv[7][a] - xv[5][a]; /* dx_C */
+    q[3][a] = xv[1][a] - xv[7][a]; /* dx_D */
+  }
+  for (int t = 0; t < 4; ++t) {
+    double c[3];
+    cross(q[t], q[(t + 1) % 4], c);
+    for (int a = 0; a < 3; ++a) nA[a] += c[a] / 4.0;
+  }
+}
+
+/* Next-nearest-neighbour current at interior node (i, j, k): the three
+ * octilaterals' vector areas as the rows of M and their circulations as c
+ * in eq. "current matrix equation", M J = c. */
+static int nnn_at(const ora_grid* g, const double* x, const double* B, int i,
+                  int j, int k, double J[3]) {
+  int ctr[3] = {i, j, k};
+  double M[9], c[3];
+  for (int r = 0; r < 3; ++r) {
+    int v[8][3];
+    double xv[8][3], Bv[8][3], nA[3];
+    octilateral_vertices(r, ctr, v);
+    for (int m = 0; m < 8; ++m) {
+      get3(g, x, v[m][0], v[m][1], v[m][2], xv[m]);
+      get3(g, B, v[m][0], v[m][1], v[m][2], Bv[m]);
+    }
+    octilateral_loop(xv, Bv, &c[r], nA);
+    for (int a = 0; a < 3; ++a) M[r * 3 + a] = nA[a];
+  }
+  return solve3(M, c, J) == 0 ? ORA_OK : ORA_ERR_COLLAPSED;
+}
+
+int ora_curl_nnn(const ora_grid* g, const double* x, const double* B,
+                 double* J) {
+  long N = n_nodes(g);
+  int rc = ORA_OK;
+  memset(J, 0, sizeof(double) * 3 * N);
+  for (int k = 1; k < g->nz - 1; ++k)
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) {
+        double Jn[3];
+        if (nnn_at(g, x, B, i, j, k, Jn) != ORA_OK) rc = ORA_ERR_COLLAPSED;
         long n = node(g, i, j, k);
         J[n] = Jn[0];
         J[N + n] = Jn[1];
@@ -429,6 +564,35 @@ int ora_curl_direct(const ora_grid* g, const double* x, const double* B0,
 
 /* ------------------------------------------------------------ velocity */
 
+/* J of the selected current at every interior node (0 elsewhere), B the
+ * pulled-back field on the same positions. */
+static int curl_of(const ora_grid* g, int curl, const double* x, const double* B0,
+                   const double* B, double* J) {
+  if (curl == ORA_CURL_DIRECT) return ora_curl_direct(g, x, B0, J);
+  if (curl == ORA_CURL_NNN) return ora_curl_nnn(g, x, B, J);
+  return ora_curl_mimetic(g, x, B, J, NULL);
+}
+
+/* B (eq. "B transformation") and J of state x; with periodic z the ghost
+ * planes of (a copy of) x are first set from the inner planes. */
+static int state_fields(const ora_grid* g, int curl, const double* x,
+                        const double* B0, double* B, double* J) {
+  long n = 3 * n_nodes(g);
+  const double* xs = x;
+  double* xc = NULL;
+  if (g->periodic_z) {
+    xc = (double*)malloc(sizeof(double) * n);
+    if (!xc) return ORA_ERR_BADARG;
+    memcpy(xc, x, sizeof(double) * n);
+    refresh_ghosts(g, xc);
+    xs = xc;
+  }
+  int rc = ora_pullback(g, xs, B0, B, NULL);
+  int rc2 = curl_of(g, curl, xs, B0, B, J);
+  free(xc);
+  return rc == ORA_OK ? rc2 : rc;
+}
+
 void ora_lorentz_velocity(const ora_grid* g, const double* J, const double* B,
                           double* u) {
   long N = n_nodes(g);
@@ -459,10 +623,7 @@ int ora_velocity(const ora_grid* g, int curl, const double* x,
     free(J);
     return ORA_ERR_BADARG;
   }
-  int rc = ora_pullback(g, x, B0, B, NULL);
-  int rc2 = curl == ORA_CURL_DIRECT ? ora_curl_direct(g, x, B0, J)
-                                    : ora_curl_mimetic(g, x, B, J, NULL);
-  if (rc == ORA_OK) rc = rc2;
+  int rc = state_fields(g, curl, x, B0, B, J);
   ora_lorentz_velocity(g, J, B, u);
   free(B);
   free(J);
@@ -471,6 +632,7 @@ int ora_velocity(const ora_grid* g, int curl, const double* x,
 
 int ora_velocity_at(const ora_grid* g, int curl, const double* x,
                     const double* B0, int i, int j, int k, double u[3]) {
+  if (g->periodic_z) return ORA_ERR_BADARG; /* whole-grid ora_velocity only */
   if (!is_interior(g, i, j, k)) {
     u[0] = u[1] = u[2] = 0.0;
     return ORA_OK;
@@ -479,6 +641,30 @@ int ora_velocity_at(const ora_grid* g, int curl, const double* x,
   if (curl == ORA_CURL_DIRECT) {
     int rc = direct_at(g, x, B0, i, j, k, J, Bc);
     if (rc != ORA_OK) return rc;
+  } else if (curl == ORA_CURL_NNN) {
+    /* B at the node's 3x3x3 neighbourhood (a small local copy) */
+    ora_grid lg = {3, 3, 3, {g->h[0], g->h[1], g->h[2]}, 0};
+    double lx[81], lB[81];
+    for (int c = 0; c < 3; ++c)
+      for (int dk = 0; dk < 3; ++dk)
+        for (int dj = 0; dj < 3; ++dj)
+          for (int di = 0; di < 3; ++di) {
+            long m = node(&lg, di, dj, dk);
+            lx[c * 27 + m] = x[c * n_nodes(g) + node(g, i + di - 1, j + dj - 1, k + dk - 1)];
+          }
+    for (int dk = 0; dk < 3; ++dk)
+      for (int dj = 0; dj < 3; ++dj)
+        for (int di = 0; di < 3; ++di) {
+          double b[3];
+          if (pullback_at(g, x, B0, i + di - 1, j + dj - 1, k + dk - 1, b, NULL) != ORA_OK)
+            return ORA_ERR_COLLAPSED;
+          long m = node(&lg, di, dj, dk);
+          for (int c = 0; c < 3; ++c) lB[c * 27 + m] = b[c];
+        }
+    int rc = nnn_at(&lg, lx, lB, 1, 1, 1, J);
+    if (rc != ORA_OK) return rc;
+    if (pullback_at(g, x, B0, i, j, k, Bc, NULL) != ORA_OK)
+      return ORA_ERR_COLLAPSED;
   } else {
     int ctr[3] = {i, j, k};
     double xv[3][4][3], Bv[3][4][3], xc[3], c[3], M[9];
@@ -613,7 +799,7 @@ static int pullback_status(const ora_grid* g, const double* x,
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
         double b[3];
-        if (pullback_at(g, x, B0, i, j, k, b, NULL) != ORA_OK)
+        if (pullback_at(g, x, B0, i, j, b_plane(g, k), b, NULL) != ORA_OK)
           return ORA_ERR_COLLAPSED;
       }
   return ORA_OK;
@@ -642,6 +828,7 @@ int ora_step_fixed(const ora_grid* g, int curl, double* x, const double* B0,
   int rc = ora_ck_attempt(n, x, dt, grid_rhs, &c, xn, er, NULL);
   if (lambda) *lambda = max_abs(n, er);
   memcpy(x, xn, sizeof(double) * n);
+  refresh_ghosts(g, x);
   free(xn);
   free(er);
   return rc;
@@ -685,6 +872,7 @@ int ora_relax(const ora_grid* g, int curl, const ora_control_opts* o,
     }
     if (accept) {
       memcpy(x, xn, sizeof(double) * n);
+      refresh_ghosts(g, x);
       t += *dt;
       if (dt_log) dt_log[acc] = *dt;
       ++acc;
@@ -713,7 +901,9 @@ int ora_energy(const ora_grid* g, const double* x, const double* B0,
                double* E) {
   double sum = 0.0;
   int rc = ORA_OK;
-  for (int k = 0; k < g->nz; ++k)
+  /* periodic in z: one period, the inner planes, none of them on a z face */
+  int k0 = g->periodic_z ? 1 : 0, k1 = g->periodic_z ? g->nz - 1 : g->nz;
+  for (int k = k0; k < k1; ++k)
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
         double B[3], D;
@@ -723,7 +913,7 @@ int ora_energy(const ora_grid* g, const double* x, const double* B0,
         double zeta = 1.0;
         if (i == 0 || i == g->nx - 1) zeta *= 0.5;
         if (j == 0 || j == g->ny - 1) zeta *= 0.5;
-        if (k == 0 || k == g->nz - 1) zeta *= 0.5;
+        if (!g->periodic_z && (k == 0 || k == g->nz - 1)) zeta *= 0.5;
         sum += zeta * dot(B, B) * D;
       }
   *E = 0.5 * sum * g->h[0] * g->h[1] * g->h[2];
@@ -740,10 +930,7 @@ int ora_forcefree(const ora_grid* g, int curl, const double* x,
     free(J);
     return ORA_ERR_BADARG;
   }
-  int rc = ora_pullback(g, x, B0, B, NULL);
-  int rc2 = curl == ORA_CURL_DIRECT ? ora_curl_direct(g, x, B0, J)
-                                    : ora_curl_mimetic(g, x, B, J, NULL);
-  if (rc == ORA_OK) rc = rc2;
+  int rc = state_fields(g, curl, x, B0, B, J);
   double m1 = 0.0, m2 = 0.0;
   for (int k = 1; k < g->nz - 1; ++k)
     for (int j = 1; j < g->ny - 1; ++j)
@@ -809,10 +996,7 @@ int ora_alpha_line(const ora_grid* g, int curl, const double* x,
     free(J);
     return ORA_ERR_BADARG;
   }
-  int rc = ora_pullback(g, x, B0, B, NULL);
-  int rc2 = curl == ORA_CURL_DIRECT ? ora_curl_direct(g, x, B0, J)
-                                    : ora_curl_mimetic(g, x, B, J, NULL);
-  if (rc == ORA_OK) rc = rc2;
+  int rc = state_fields(g, curl, x, B0, B, J);
   alpha[0] = alpha[g->nz - 1] = NAN;
   for (int k = 1; k < g->nz - 1; ++k) {
     double Jn[3], Bn[3];

@@ -29,9 +29,16 @@ extern "C" {
 typedef struct {
   int nx, ny, nz;
   double h[3];
+  /* 0: line-tied on every face (section "Boundary Conditions").  1: periodic
+   * in z: planes k = 0 and k = nz-1 are ghosts of the last and first inner
+   * planes shifted by the period L_z + dZ = (nz - 2) h_z along z,
+   * x(i,j,0) = x(i,j,nz-2) - (L_z + dZ) e_z and x(i,j,nz-1) = x(i,j,1) +
+   * (L_z + dZ) e_z, so that B is periodic; the x and y faces stay
+   * line-tied.  B0 must be periodic with the same period. */
+  int periodic_z;
 } ora_grid;
 
-enum { ORA_CURL_MIMETIC = 0, ORA_CURL_DIRECT = 1 };
+enum { ORA_CURL_MIMETIC = 0, ORA_CURL_DIRECT = 1, ORA_CURL_NNN = 2 };
 
 enum {
   ORA_OK = 0,
@@ -86,6 +93,14 @@ int ora_mimetic_loops_at(const ora_grid* g, const double* x, const double* B,
  * of B0), at every interior node (0 elsewhere). */
 int ora_curl_direct(const ora_grid* g, const double* x, const double* B0,
                     double* J);
+
+/* Section "Next Nearest Neighbor Mimetic Approach": the octilateral loops
+ * through the eight in-plane neighbours (face and edge-diagonal) of each
+ * index surface, eqs. "eight surfaces" / "sum of eight triangles" for
+ * their vector areas, M J = c (eq. "current matrix equation") at every
+ * interior node (0 elsewhere). */
+int ora_curl_nnn(const ora_grid* g, const double* x, const double* B,
+                 double* J);
 
 /* u = J x B (gamma = 1) at interior nodes, u = 0 on line-tied boundary
  * nodes (eq. "magneto friction"; section "Boundary Conditions"). */

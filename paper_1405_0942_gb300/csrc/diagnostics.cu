@@ -32,6 +32,7 @@ namespace {
 struct DG {
   int nx, ny, nz;
   double lo[3], h[3], h2[3];
+  int periodic;  // periodic in z: ghost planes carry their partner's B
 };
 
 __device__ __forceinline__ int nid(const DG& g, int i, int j, int k) {
@@ -72,9 +73,12 @@ __device__ __forceinline__ double ddet(const double g0[3], const double g1[3],
 }
 
 // Eq. "B transformation" at node (i, j, k): B and det G; G's columns in g.
+// Periodic in z, a ghost plane's B is its partner's (section "Boundary
+// Conditions").
 template <typename T>
 __device__ double pull_B(const DG& g, const T* d, const T* B0s, int N, int i, int j, int k,
                          double G[3][3], double B[3]) {
+  if (g.periodic) k = k == 0 ? g.nz - 2 : (k == g.nz - 1 ? 1 : k);
   gcol_d(g, d, N, 0, i, j, k, G[0]);
   gcol_d(g, d, N, 1, i, j, k, G[1]);
   gcol_d(g, d, N, 2, i, j, k, G[2]);
@@ -104,6 +108,77 @@ __device__ void current_mimetic(const DG& g, const T* d, const T* B0s, int N, in
     cc[a] = ddot(P[a1], G[a2]) - ddot(P[a2], G[a1]);
   }
   for (int c = 0; c < 3; ++c) J[c] = (cc[0] * G[0][c] + cc[1] * G[1][c] + cc[2] * G[2][c]) / det;
+}
+
+// Next-nearest-neighbour current at interior node (i, j, k): in each index
+// surface r (spanned by p = r+1, q = r+2) the octilateral through the eight
+// in-plane neighbours, counter-clockwise about +r from the corner
+// +e_p - e_q, edge-mean B for the circulation, the four corner triangles
+// (/ 2) and the inner quadrilateral through the face neighbours (/ 4) for
+// the vector area; M J = c solved by the adjugate.
+template <typename T>
+__device__ void current_nnn(const DG& g, const T* d, const T* B0s, int N, int i, int j, int k,
+                            double J[3], double B[3]) {
+  const int op[8] = {1, 1, 1, 0, -1, -1, -1, 0};
+  const int oq[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
+  const int n = nid(g, i, j, k);
+  double Gc[3][3], M[3][3], cr[3];
+  pull_B(g, d, B0s, N, i, j, k, Gc, B);
+  for (int r = 0; r < 3; ++r) {
+    const int p = (r + 1) % 3, q = (r + 2) % 3;
+    double xv[8][3], Bv[8][3], Gn[3][3];
+    for (int m = 0; m < 8; ++m) {
+      int id[3] = {i, j, k};
+      id[p] += op[m];
+      id[q] += oq[m];
+      const int nn = nid(g, id[0], id[1], id[2]);
+      for (int c = 0; c < 3; ++c) xv[m][c] = (double)d[c * N + nn] - (double)d[c * N + n];
+      xv[m][p] += op[m] * g.h[p];
+      xv[m][q] += oq[m] * g.h[q];
+      pull_B(g, d, B0s, N, id[0], id[1], id[2], Gn, Bv[m]);
+    }
+    double circ = 0.0, dx[8][3];
+    for (int m = 0; m < 8; ++m)
+      for (int c = 0; c < 3; ++c) {
+        dx[m][c] = xv[(m + 1) % 8][c] - xv[m][c];
+        circ += 0.5 * (Bv[m][c] + Bv[(m + 1) % 8][c]) * dx[m][c];
+      }
+    double area[3] = {0.0, 0.0, 0.0};
+    for (int t = 0; t < 4; ++t) {
+      const double* e0 = dx[2 * t + 1];
+      const double* e1 = dx[(2 * t + 2) % 8];
+      area[0] += 0.5 * (e0[1] * e1[2] - e0[2] * e1[1]);
+      area[1] += 0.5 * (e0[2] * e1[0] - e0[0] * e1[2]);
+      area[2] += 0.5 * (e0[0] * e1[1] - e0[1] * e1[0]);
+    }
+    double qd[4][3];
+    for (int c = 0; c < 3; ++c) {
+      qd[0][c] = xv[3][c] - xv[1][c];
+      qd[1][c] = xv[5][c] - xv[3][c];
+      qd[2][c] = xv[7][c] - xv[5][c];
+      qd[3][c] = xv[1][c] - xv[7][c];
+    }
+    for (int t = 0; t < 4; ++t) {
+      const double* e0 = qd[t];
+      const double* e1 = qd[(t + 1) % 4];
+      area[0] += 0.25 * (e0[1] * e1[2] - e0[2] * e1[1]);
+      area[1] += 0.25 * (e0[2] * e1[0] - e0[0] * e1[2]);
+      area[2] += 0.25 * (e0[0] * e1[1] - e0[1] * e1[0]);
+    }
+    cr[r] = circ;
+    for (int c = 0; c < 3; ++c) M[r][c] = area[c];
+  }
+  double adj[3][3];
+  for (int r = 0; r < 3; ++r) {
+    const double* u = M[(r + 1) % 3];
+    const double* v = M[(r + 2) % 3];
+    adj[r][0] = u[1] * v[2] - u[2] * v[1];
+    adj[r][1] = u[2] * v[0] - u[0] * v[2];
+    adj[r][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double detM = ddot(M[0], adj[0]);
+  for (int c = 0; c < 3; ++c)
+    J[c] = (cr[0] * adj[0][c] + cr[1] * adj[1][c] + cr[2] * adj[2][c]) / detM;
 }
 
 // Classic current at interior node (i, j, k): dB/dX by the product rule on
@@ -257,6 +332,8 @@ __global__ void __launch_bounds__(DT) k_alpha_line(DG g, const void* const* dbuf
       double J[3], B[3];
       if (CURL == GLEMUR_CURL_DIRECT)
         current_direct(g, d, B0s, N, i, j, k, J, B);
+      else if (CURL == GLEMUR_CURL_NNN)
+        current_nnn(g, d, B0s, N, i, j, k, J, B);
       else
         current_mimetic(g, d, B0s, N, i, j, k, J, B);
       a = ddot(J, B) / ddot(B, B);
@@ -332,6 +409,7 @@ DG geom_of(const DiagCtx& c) {
     g.h[a] = c.h[a];
     g.h2[a] = 2.0 * c.h[a];
   }
+  g.periodic = c.periodic;
   return g;
 }
 
@@ -396,7 +474,10 @@ int glemur_alpha_line(glemur_ctx* ctx, int i, int j, double a_r, double* alpha,
   const DG g = geom_of(c);
   const size_t sm = sizeof(double) * c.nz;
   const bool direct = c.curl == GLEMUR_CURL_DIRECT;
-  if (c.precision == GLEMUR_MIXED) {
+  if (c.curl == GLEMUR_CURL_NNN) {  // FP64 contexts only
+    k_alpha_line<double, 2><<<1, DT, sm, c.s>>>(g, c.dbuf_dev, c.st, (const double*)c.B0s, i, j,
+                                                a_r, c.stage);
+  } else if (c.precision == GLEMUR_MIXED) {
     if (direct)
       k_alpha_line<float, 1><<<1, DT, sm, c.s>>>(g, c.dbuf_dev, c.st, (const float*)c.B0s, i, j,
                                                  a_r, c.stage);

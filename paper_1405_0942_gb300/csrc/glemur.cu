@@ -34,8 +34,8 @@ cudaError_t prepare_f32_mimetic_tma();
 int ctas_per_sm_f32_mimetic_tma();
 int tile_rows_f32_mimetic_tma();
 
-cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s);
-void split_ctas_per_sm(int b[6], int c[6]);
+cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s, int curl);
+void split_ctas_per_sm(int b[6], int c[6], int curl);
 
 // Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
 // of section "Time Stepping".
@@ -281,6 +281,7 @@ __global__ void k_control(DevState* st, const double* part, int nb, int diag, do
 struct GridGeom {
   int nx, ny, nz;
   double lo[3], h[3];
+  int periodic;  // periodic in z (ghost planes 0 and nz-1)
 };
 
 __device__ __forceinline__ double label(const GridGeom& g, int a, int i) {
@@ -295,9 +296,13 @@ __global__ void k_set_x(GridGeom g, const double* __restrict__ x, T* d0, T* d1, 
   const int N = g.nx * g.ny * g.nz;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     const int i = n % g.nx, r = n / g.nx, j = r % g.ny, k = r / g.ny;
-    const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, k)};
+    // periodic in z: a ghost plane takes its partner's displacement (the
+    // ghost's position is the partner's shifted by the period)
+    const int ks = g.periodic && k == 0 ? g.nz - 2 : (g.periodic && k == g.nz - 1 ? 1 : k);
+    const int ns = (ks * g.ny + j) * g.nx + i;
+    const double X[3] = {label(g, 0, i), label(g, 1, j), label(g, 2, ks)};
     for (int c = 0; c < 3; ++c) {
-      const T v = (T)(x[c * N + n] - X[c]);
+      const T v = (T)(x[c * N + ns] - X[c]);
       d0[c * N + n] = v;
       d1[c * N + n] = v;
       y0[c * N + n] = v;
@@ -417,6 +422,7 @@ GridGeom geom(const glemur_ctx* c) {
     g.lo[a] = c->lo[a];
     g.h[a] = c->h[a];
   }
+  g.periodic = c->o.periodic_z;
   return g;
 }
 
@@ -482,7 +488,8 @@ int nblocks_of(const glemur_ctx* c, int curl) {
   return curl == GLEMUR_CURL_DIRECT ? c->nblocks_direct : c->nblocks;
 }
 
-cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, void* k6) {
+cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, void* k6,
+                         int curl) {
   SplitArgs a;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -500,6 +507,7 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.Gb = c->Gb;
   a.diag = diag;
   a.force = force;
+  a.periodic = c->o.periodic_z;
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
@@ -507,12 +515,14 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
     a.grid_b[j] = c->split_grid_b[j];
     a.grid_c[j] = c->split_grid_c[j];
   }
-  return launch_f64_split(a, stage, c->s);
+  return launch_f64_split(a, stage, c->s, curl == GLEMUR_CURL_NNN ? 2 : 0);
 }
 
 cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force,
                          void* k6 = nullptr) {
-  if (c->split && curl == GLEMUR_CURL_MIMETIC) return launch_split(c, stage, diag, force, k6);
+  if (c->split && curl != GLEMUR_CURL_DIRECT)
+    return launch_split(c, stage, diag, force, k6, curl);
+  if (curl == GLEMUR_CURL_NNN) return cudaErrorInvalidValue;  // FP64 two-pass only
   const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
   if (c->o.precision == GLEMUR_MIXED) {
     StageArgs<float> a = make_args<float>(c, stage, diag, force);
@@ -727,6 +737,7 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
     a.Gb = c->Gb;
     a.diag = 0;
     a.force = 1;
+    a.periodic = 0;  // the adjoint refuses periodic contexts (ctx_info)
     a.st = c->st;
     a.part = c->part;
     a.nblocks = c->nblocks;
@@ -734,7 +745,7 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
       a.grid_b[j] = c->split_grid_b[j];
       a.grid_c[j] = c->split_grid_c[j];
     }
-    e = launch_f64_split(a, s, c->s);
+    e = launch_f64_split(a, s, c->s, 0);
   }
   return cuda_rc(e);
 }
@@ -742,6 +753,7 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
 // Geometry, storage and the current accepted displacement (synchronises).
 int ctx_info(glemur_ctx* c, int* nx, int* ny, int* nz, double h[3], int* precision,
              void** d_cur, void** B0s, void** k, void** stream) {
+  if (c->o.periodic_z) return GLEMUR_ERR_BADARG;  // no adjoint of the periodic step
   DevState hs;
   int rc = read_state(c, &hs);
   if (rc) return rc;
@@ -768,6 +780,7 @@ int ctx_diag(glemur_ctx* c, DiagCtx* o) {
   }
   o->precision = c->o.precision;
   o->curl = c->o.curl;
+  o->periodic = c->o.periodic_z;
   o->dbuf_dev = (const void* const*)c->dbuf_dev;
   o->B0s = c->B0s;
   o->st = c->st;
@@ -794,6 +807,7 @@ void glemur_default_opts(glemur_opts* o) {
   o->max_rejects = 64;
   o->diag_each_attempt = 1;
   o->safety = 1.0;
+  o->periodic_z = 0;
 }
 
 size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision) {
@@ -811,7 +825,11 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   glemur_default_opts(&o);
   if (opts) o = *opts;
   if ((o.precision != GLEMUR_FP64 && o.precision != GLEMUR_MIXED) ||
-      (o.curl != GLEMUR_CURL_MIMETIC && o.curl != GLEMUR_CURL_DIRECT) ||
+      (o.curl != GLEMUR_CURL_MIMETIC && o.curl != GLEMUR_CURL_DIRECT &&
+       o.curl != GLEMUR_CURL_NNN) ||
+      (o.curl == GLEMUR_CURL_NNN && o.precision != GLEMUR_FP64) ||
+      (o.periodic_z != 0 && o.periodic_z != 1) ||
+      (o.periodic_z && (o.precision != GLEMUR_FP64 || o.curl == GLEMUR_CURL_DIRECT)) ||
       !(o.lambda0 > 0) || !(o.dt0 > 0) || !(o.dt_min >= 0) || !(o.grow_max >= 1) ||
       !(o.shrink_min > 0 && o.shrink_min <= 1) || o.max_rejects < 0 ||
       !(o.safety > 0 && o.safety <= 1))
@@ -859,7 +877,8 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
     c->rb = (double*)p; p += align256((size_t)c->N * 8);
     c->Gb = (double*)p;
     const char* fused = getenv("GLEMUR_F64_FUSED");
-    c->split = !(fused && atoi(fused) > 0);
+    // the next-nearest-neighbour current exists in the two-pass form only
+    c->split = o.curl == GLEMUR_CURL_NNN || o.periodic_z || !(fused && atoi(fused) > 0);
   }
 
   int dev = 0;
@@ -898,7 +917,7 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
     // per pass one wave of CTAs of 256 threads, each over an equal range of
     // node warps; the partials' stride is the larger grid
     int ob[6], oc[6];
-    split_ctas_per_sm(ob, oc);
+    split_ctas_per_sm(ob, oc, o.curl == GLEMUR_CURL_NNN ? 2 : 0);
     const long long need = (c->N + 255) / 256;
     c->nblocks = 1;
     for (int s = 0; s < 6; ++s) {
@@ -1124,7 +1143,7 @@ int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
 }
 
 int glemur_kernels_per_attempt(const glemur_ctx* c) {
-  return c ? (c->split && c->o.curl == GLEMUR_CURL_MIMETIC ? 13 : 7) : 0;
+  return c ? (c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 13 : 7) : 0;
 }
 
 int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {

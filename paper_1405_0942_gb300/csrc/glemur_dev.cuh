@@ -162,6 +162,7 @@ struct SplitArgs {
                        // interior node, 9N: component c of g_a at
                        // Gb[(3a + c) N + n] (written by pass B, read by C)
   int diag, force;
+  int periodic;        // periodic in z: planes 0, nz-1 are ghosts of nz-2, 1
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;         // partial stride: the largest of the grids
@@ -173,7 +174,7 @@ struct SplitArgs {
 struct DiagCtx {
   int nx, ny, nz;
   double lo[3], h[3];
-  int precision, curl;
+  int precision, curl, periodic;
   const void* const* dbuf_dev;  // device copy of the two displacement buffers
   const void* B0s;              // pre-scaled B0 in storage precision
   const DevState* st;           // .cur selects the accepted displacement

@@ -104,13 +104,14 @@ __device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __r
 }
 
 // B and 1/det G at node n = (i, j, k) from the stage input y (eq. "B
-// transformation"); returns the node's energy term zeta |B|^2 det G if
+// transformation"), stored at node nw (n itself, or a periodic ghost node
+// that carries n's B); returns the node's energy term zeta |B|^2 det G if
 // `energy`.  FACE: the general stencil (one-sided differences on the
 // boundary faces the node touches), else central differences only.
 template <bool FACE>
 __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double* __restrict__ y,
                                                int N, int n, int i, int j, int k, bool state,
-                                               bool energy) {
+                                               bool energy, int nw) {
   double g0[3], g1[3], g2[3];
   if (FACE) {
     split_gcol(a, y, N, n, 0, i, a.nx, 1, g0);
@@ -145,9 +146,9 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     B[c] = (g0[c] * b0 + g1[c] * b1 + g2[c] * b2) * r;
-    a.Bb[c * N + n] = B[c];
+    a.Bb[c * N + nw] = B[c];
   }
-  a.rb[n] = r;
+  a.rb[nw] = r;
   if (!energy) return 0.0;
   // eq. "magnetic energy": zeta halves per boundary index coordinate
   const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) + (k == 0 || k == a.nz - 1);
@@ -200,13 +201,21 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
     const int n = interior_node(a, t, i, j, k);
-    eacc += split_B_node<false>(a, y, N, n, i, j, k, S == 0, energy);
+    eacc += split_B_node<false>(a, y, N, n, i, j, k, S == 0, energy, n);
   }
   cta_range(N - NI, tb, te);
   for (int b = tb + threadIdx.x; b < te; b += blockDim.x) {
     int i, j, k;
     const int n = boundary_node(a, b, i, j, k);
-    eacc += split_B_node<true>(a, y, N, n, i, j, k, S == 0, energy);
+    if (a.periodic && (k == 0 || k == a.nz - 1)) {
+      // a ghost plane carries its partner's B (section "Boundary
+      // Conditions"); it is not part of the period's energy
+      const int kk = k == 0 ? a.nz - 2 : 1;
+      const int np = (kk * a.ny + j) * a.nx + i;
+      split_B_node<true>(a, y, N, np, i, j, kk, S == 0, false, n);
+    } else {
+      eacc += split_B_node<true>(a, y, N, n, i, j, k, S == 0, energy, n);
+    }
   }
   pdl_trigger();
   if (energy) {
@@ -215,12 +224,106 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   }
 }
 
+// The next-nearest-neighbour current (section "Next Nearest Neighbor
+// Mimetic Approach") at interior node n and B there: in each index surface
+// r (spanned by p = r+1, q = r+2 mod 3) the loop through the eight in-plane
+// neighbours, counter-clockwise about +r from the corner +e_p - e_q, with
+// edge-mean B for the circulation (eq. "current discrete" with eight
+// contributions) and, for the vector area (eq. "sum of eight triangles"),
+// the four corner triangles (edges meeting at the corners, / 2) plus the
+// inner quadrilateral through the face neighbours (/ 4); the three areas
+// are the rows of M in eq. "current matrix equation", solved here by the
+// adjugate, J = (c_0 a_1 x a_2 + c_1 a_2 x a_0 + c_2 a_0 x a_1) / det M.
+// Positions are taken relative to the node: y (displacement) differences
+// plus the label offsets.
+__device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __restrict__ y,
+                                            int N, int n, double J[3], double B[3]) {
+  const int st[3] = {1, a.nx, a.nx * a.ny};
+  double yc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) yc[c] = __ldg(&y[c * N + n]);
+  double M[3][3], cr[3];
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    const int p = (r + 1) % 3, q = (r + 2) % 3;
+    // vertex offsets (along p, along q) of V1 .. V8
+    const int op[8] = {1, 1, 1, 0, -1, -1, -1, 0};
+    const int oq[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
+    double xv[8][3], Bv[8][3];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int nn = n + op[m] * st[p] + oq[m] * st[q];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xv[m][c] = __ldg(&y[c * N + nn]) - yc[c];
+        Bv[m][c] = __ldg(&a.Bb[c * N + nn]);
+      }
+      xv[m][p] += 0.5 * op[m] * a.h2[p];
+      xv[m][q] += 0.5 * oq[m] * a.h2[q];
+    }
+    double circ = 0.0, dx[8][3];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int m1 = (m + 1) & 7;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dx[m][c] = xv[m1][c] - xv[m][c];
+        circ = fma(0.5 * (Bv[m][c] + Bv[m1][c]), dx[m][c], circ);
+      }
+    }
+    double area[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {  // corner triangles: (dx_2, dx_3), ..., (dx_8, dx_1)
+      const double* e0 = dx[2 * t + 1];
+      const double* e1 = dx[(2 * t + 2) & 7];
+      area[0] += 0.5 * (e0[1] * e1[2] - e0[2] * e1[1]);
+      area[1] += 0.5 * (e0[2] * e1[0] - e0[0] * e1[2]);
+      area[2] += 0.5 * (e0[0] * e1[1] - e0[1] * e1[0]);
+    }
+    double qd[4][3];  // inner quadrilateral V2 -> V4 -> V6 -> V8
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qd[0][c] = xv[3][c] - xv[1][c];
+      qd[1][c] = xv[5][c] - xv[3][c];
+      qd[2][c] = xv[7][c] - xv[5][c];
+      qd[3][c] = xv[1][c] - xv[7][c];
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double* e0 = qd[t];
+      const double* e1 = qd[(t + 1) & 3];
+      area[0] += 0.25 * (e0[1] * e1[2] - e0[2] * e1[1]);
+      area[1] += 0.25 * (e0[2] * e1[0] - e0[0] * e1[2]);
+      area[2] += 0.25 * (e0[0] * e1[1] - e0[1] * e1[0]);
+    }
+    cr[r] = circ;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[r][c] = area[c];
+  }
+  double adj[3][3];  // adj[r] = a_{r+1} x a_{r+2}
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double* u = M[(r + 1) % 3];
+    const double* v = M[(r + 2) % 3];
+    adj[r][0] = u[1] * v[2] - u[2] * v[1];
+    adj[r][1] = u[2] * v[0] - u[0] * v[2];
+    adj[r][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double detM = dot3(M[0], adj[0]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    J[c] = (cr[0] * adj[0][c] + cr[1] * adj[1][c] + cr[2] * adj[2][c]) / detM;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) B[c] = __ldg(&a.Bb[c * N + n]);
+}
+
 // Pass C (stage s): current and velocity at interior nodes; k_s and the
-// next stage input, or (s = 5) the update, the error and k6.  Held to 64
-// registers (a few spilled values in two of the stages): four CTAs (32
-// warps) per SM instead of three, at no measured cost.
-template <int S>
-__global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
+// next stage input, or (s = 5) the update, the error and k6.  CURL 0: the
+// nearest-neighbour current, held to 64 registers (four CTAs, 32 warps, per
+// SM); CURL 2: the next-nearest-neighbour current (a comparison option,
+// two CTAs per SM).
+template <int S, int CURL>
+__global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitArgs a) {
   constexpr bool FINAL = S == 5;
   pdl_wait();
   const DevState* st = a.st;
@@ -242,25 +345,29 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
   for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
     const int n = interior_node(a, t, i, j, k);
-    double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3], B[3];
+    double J[3], B[3], u[3];
+    if constexpr (CURL == 2) {
+      nnn_current(a, S == 0 ? d : a.ys[S & 1], N, n, J, B);
+    } else {
+      double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double* b = a.Bb + c * N;
-      g0[c] = __ldg(&a.Gb[(size_t)c * N + n]);
-      g1[c] = __ldg(&a.Gb[(size_t)(3 + c) * N + n]);
-      g2[c] = __ldg(&a.Gb[(size_t)(6 + c) * N + n]);
-      P0[c] = __ldg(&b[n + 1]) - __ldg(&b[n - 1]);
-      P1[c] = __ldg(&b[n + sy]) - __ldg(&b[n - sy]);
-      P2[c] = __ldg(&b[n + sz]) - __ldg(&b[n - sz]);
-      B[c] = __ldg(&b[n]);
+      for (int c = 0; c < 3; ++c) {
+        const double* b = a.Bb + c * N;
+        g0[c] = __ldg(&a.Gb[(size_t)c * N + n]);
+        g1[c] = __ldg(&a.Gb[(size_t)(3 + c) * N + n]);
+        g2[c] = __ldg(&a.Gb[(size_t)(6 + c) * N + n]);
+        P0[c] = __ldg(&b[n + 1]) - __ldg(&b[n - 1]);
+        P1[c] = __ldg(&b[n + sy]) - __ldg(&b[n - sy]);
+        P2[c] = __ldg(&b[n + sz]) - __ldg(&b[n - sz]);
+        B[c] = __ldg(&b[n]);
+      }
+      const double c0 = dot3_sub(P1, g2, P2, g1);
+      const double c1 = dot3_sub(P2, g0, P0, g2);
+      const double c2 = dot3_sub(P0, g1, P1, g0);
+      const double r = __ldg(&a.rb[n]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
     }
-    const double c0 = dot3_sub(P1, g2, P2, g1);
-    const double c1 = dot3_sub(P2, g0, P0, g2);
-    const double c2 = dot3_sub(P0, g1, P1, g0);
-    const double r = __ldg(&a.rb[n]);
-    double J[3], u[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
     u[0] = J[1] * B[2] - J[2] * B[1];
     u[1] = J[2] * B[0] - J[0] * B[2];
     u[2] = J[0] * B[1] - J[1] * B[0];
@@ -275,6 +382,10 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
         for (int jj = 0; jj < S; ++jj) v = fma(an[jj], __ldg(&a.k[jj][c * N + n]), v);
         v = fma(an[S], u[c], v);
         ynext[c * N + n] = v;
+        // periodic in z: the ghost of an end plane holds the same
+        // displacement (its position differs by the period)
+        if (a.periodic && (k == 1 || k == a.nz - 2))
+          ynext[c * N + n + (k == 1 ? 1 : -1) * (a.nz - 2) * sz] = v;
       }
     } else {
       const double b0 = st->dtb[0], b2 = st->dtb[2], b3 = st->dtb[3], b5 = st->dtb[5];
@@ -293,7 +404,10 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
         er = fma(e3, k4, er);
         er = fma(e4, k5, er);
         er = fma(e5, u[c], er);
-        dout[c * N + n] = __ldg(&d[c * N + n]) + up;
+        const double dn = __ldg(&d[c * N + n]) + up;
+        dout[c * N + n] = dn;
+        if (a.periodic && (k == 1 || k == a.nz - 2))
+          dout[c * N + n + (k == 1 ? 1 : -1) * (a.nz - 2) * sz] = dn;
         acc.max_lam(fabs(er));
         if (a.k[5]) a.k[5][c * N + n] = u[c];
       }
@@ -312,12 +426,16 @@ __global__ void __launch_bounds__(256, 4) k_split_C(const SplitArgs a) {
   }
 }
 
-// CTAs of 256 threads per SM that pass B and pass C of each stage can hold.
-void split_ctas_per_sm(int b[6], int c[6]) {
+// CTAs of 256 threads per SM that pass B and pass C of each stage can hold
+// (pass C with the current `curl`: 0 nearest, 2 next-nearest neighbours).
+void split_ctas_per_sm(int b[6], int c[6], int curl) {
   void (*kb[6])(const SplitArgs) = {k_split_B<0>, k_split_B<1>, k_split_B<2>,
                                     k_split_B<3>, k_split_B<4>, k_split_B<5>};
-  void (*kc[6])(const SplitArgs) = {k_split_C<0>, k_split_C<1>, k_split_C<2>,
-                                    k_split_C<3>, k_split_C<4>, k_split_C<5>};
+  void (*kc0[6])(const SplitArgs) = {k_split_C<0, 0>, k_split_C<1, 0>, k_split_C<2, 0>,
+                                     k_split_C<3, 0>, k_split_C<4, 0>, k_split_C<5, 0>};
+  void (*kc2[6])(const SplitArgs) = {k_split_C<0, 2>, k_split_C<1, 2>, k_split_C<2, 2>,
+                                     k_split_C<3, 2>, k_split_C<4, 2>, k_split_C<5, 2>};
+  void (**kc)(const SplitArgs) = curl == 2 ? kc2 : kc0;
   for (int s = 0; s < 6; ++s) {
     b[s] = c[s] = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[s], kb[s], 256, 0);
@@ -327,15 +445,18 @@ void split_ctas_per_sm(int b[6], int c[6]) {
   }
 }
 
-// Launch both passes of stage s (grid_b[s], grid_c[s] CTAs of 256 threads).
-cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s) {
-  if (stage < 0 || stage > 5) return cudaErrorInvalidValue;
+// Launch both passes of stage s (grid_b[s], grid_c[s] CTAs of 256 threads)
+// with the current `curl` (0 nearest, 2 next-nearest neighbours).
+cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s, int curl) {
+  if (stage < 0 || stage > 5 || (curl != 0 && curl != 2)) return cudaErrorInvalidValue;
   const dim3 gb(a.grid_b[stage]), gc(a.grid_c[stage]);
   cudaError_t e = cudaSuccess;
-#define GLEMUR_SPLIT_CASE(SS)                                                      \
-  case SS:                                                                         \
-    e = launch_pdl(k_split_B<SS>, gb, dim3(256), 0, s, a);                         \
-    if (e == cudaSuccess) e = launch_pdl(k_split_C<SS>, gc, dim3(256), 0, s, a);   \
+#define GLEMUR_SPLIT_CASE(SS)                                                          \
+  case SS:                                                                             \
+    e = launch_pdl(k_split_B<SS>, gb, dim3(256), 0, s, a);                             \
+    if (e == cudaSuccess)                                                              \
+      e = curl == 2 ? launch_pdl(k_split_C<SS, 2>, gc, dim3(256), 0, s, a)             \
+                    : launch_pdl(k_split_C<SS, 0>, gc, dim3(256), 0, s, a);            \
     break;
   switch (stage) {
     GLEMUR_SPLIT_CASE(0)

@@ -20,7 +20,7 @@ OK = 0
 ERR = {-1: "BADARG", -2: "CUDA", -3: "COLLAPSED", -4: "NONFINITE", -5: "DT_UNDERFLOW",
        -6: "WORKSPACE", -7: "TOO_LARGE", -8: "TIMEOUT"}
 FP64, MIXED = 0, 1
-MIMETIC, DIRECT = 0, 1
+MIMETIC, DIRECT, NNN = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 
 
@@ -34,7 +34,8 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("curl", C.c_int), ("lambda0", C.c_double),
                 ("dt0", C.c_double), ("dt_min", C.c_double), ("grow_max", C.c_double),
                 ("shrink_min", C.c_double), ("max_rejects", C.c_int),
-                ("diag_each_attempt", C.c_int), ("safety", C.c_double)]
+                ("diag_each_attempt", C.c_int), ("safety", C.c_double),
+                ("periodic_z", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -161,7 +162,7 @@ class Relaxation:
     def __init__(self, nx, ny, nz, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
                  precision=FP64, curl=MIMETIC, lambda0=None, dt0=None, dt_min=None,
                  grow_max=None, shrink_min=None, max_rejects=None, diag_each_attempt=None,
-                 safety=None, device=None, stream=None):
+                 safety=None, periodic_z=None, device=None, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the GB300 relaxation library needs a CUDA device")
@@ -173,7 +174,7 @@ class Relaxation:
         for name, v in (("lambda0", lambda0), ("dt0", dt0), ("dt_min", dt_min),
                         ("grow_max", grow_max), ("shrink_min", shrink_min),
                         ("max_rejects", max_rejects), ("diag_each_attempt", diag_each_attempt),
-                        ("safety", safety)):
+                        ("safety", safety), ("periodic_z", periodic_z)):
             if v is not None:
                 setattr(o, name, type(getattr(o, name))(v))
         self.opts = o

@@ -1,0 +1,91 @@
+"""The next-nearest-neighbour (octilateral) current of section "Next
+Nearest Neighbor Mimetic Approach" (GLEMUR_CURL_NNN, FP64 two-pass stages)
+against the FP64 oracle: velocities, one Cash-Karp step (also at the 64^3
+benchmark size, where threads take several nodes), the force-free
+diagnostics and alpha* along a node line.  Tolerances as for the
+nearest-neighbour current (tests/test_gpu_parity.py)."""
+import math
+
+import numpy as np
+import pytest
+
+import glemur_inputs as gi
+import oracle as ora
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1405_0942_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def braid_case(nx, ny, nz):
+    g = gi.Grid(nx, ny, nz)
+    X = gi.nodes(g)
+    return g, gi.predistort(X, 2), gi.braid_field(X, gi.braid_regions(6, None, True))
+
+
+def relaxation(G, g, x0, B0, **kw):
+    r = G.Relaxation(g.nx, g.ny, g.nz, g.lo, g.hi, curl=G.NNN, **kw)
+    r.set_x(torch.from_numpy(np.ascontiguousarray(x0)).cuda())
+    r.set_B0(torch.from_numpy(np.ascontiguousarray(B0)).cuda())
+    return r
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (16, 16, 16), (37, 19, 23)],
+                         ids=lambda d: "x".join(map(str, d)))
+def test_velocity_nnn(G, dims):
+    g, x0, B0 = braid_case(*dims)
+    r = relaxation(G, g, x0, B0)
+    u = r.velocity().cpu().numpy()
+    u_ref, rc = ora.velocity(g, x0, B0, ora.NNN)
+    assert rc == ora.OK
+    assert rel_inf(u, u_ref) < 1e-11
+    ub = u.copy()
+    ub[:, 1:-1, 1:-1, 1:-1] = 0
+    assert np.all(ub == 0)
+
+
+@pytest.mark.parametrize("dims", [(24, 20, 28), (64, 64, 64)], ids=lambda d: "x".join(map(str, d)))
+def test_one_step_nnn(G, dims):
+    g, x0, B0 = braid_case(*dims)
+    dt = 3e-4
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, ora.NNN)
+    assert rc == ora.OK
+    r = relaxation(G, g, x0, B0)
+    st = r.step_fixed(dt)
+    assert st["accepted"] == 1
+    x = r.get_x().cpu().numpy()
+    assert rel_inf(x, x_ref) < 1e-12
+    assert np.abs(x - x_ref).max() < 1e-9 * np.abs(x_ref - x0).max()
+    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref
+
+
+def test_diagnostics_nnn(G):
+    g, x0, B0 = braid_case(29, 17, 21)
+    r = relaxation(G, g, x0, B0)
+    xi_ref, xis_ref, _ = ora.forcefree(g, x0, B0, ora.NNN)
+    xi, xis = r.forcefree_err()
+    assert abs(xi - xi_ref) < 1e-10 * xi_ref and abs(xis - xis_ref) < 1e-10 * xis_ref
+    E_ref, _ = ora.energy(g, x0, B0)
+    assert abs(r.energy() - E_ref) < 1e-13 * E_ref
+    a, e = r.alpha_line(14, 8, math.sqrt(2.0))
+    a_o, e_o, rc = ora.alpha_line(g, x0, B0, 14, 8, math.sqrt(2.0), ora.NNN)
+    assert np.abs(a[1:-1] - a_o[1:-1]).max() <= 1e-10 * np.abs(a_o[1:-1]).max()
+    assert abs(e - e_o) <= 1e-8 * e_o
+
+
+def test_nnn_is_fp64_only(G):
+    with pytest.raises(G.GlemurError):
+        G.Relaxation(8, 8, 8, precision=G.MIXED, curl=G.NNN)
