@@ -445,7 +445,7 @@ def our_arm(args):
     barrier()
     sampler.start()
     r, whole, split, st = time_mode(G, torch, w, args.precision, args.curl, args.steps,
-                                    args.warmup, flush)
+                                    args.warmup, flush, args.min_seconds)
     barrier()
     clocks = sampler.stop()
     # device time of every timed attempt; slowest rank, units of all ranks
@@ -461,7 +461,7 @@ def our_arm(args):
             if (prec, curl) == (args.precision, args.curl):
                 continue
             _, ms2, sp2, st2 = time_mode(G, torch, w, prec, curl, args.steps, args.warmup,
-                                         flush)
+                                         flush, args.min_seconds)
             v2 = w.grid.n_interior * 6 / (ms2.mean() * 1e-3)
             extra[f"{prec}_{curl}"] = {
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.mean(),
@@ -474,7 +474,7 @@ def our_arm(args):
             for name in ("braid128", "prod384"):
                 wl = workload(name)
                 r3, ms3, sp3, _ = time_mode(G, torch, wl, "mixed", "mimetic", args.steps,
-                                            args.warmup, flush)
+                                            args.warmup, flush, args.min_seconds)
                 v3 = wl.grid.n_interior * 6 / (ms3.mean() * 1e-3)
                 extra[f"mixed_mimetic_{name}"] = {
                     "value": v3, "unit": UNIT, "ms_per_step": ms3.mean(),
@@ -556,6 +556,9 @@ def main():
                     help="time only the reverse step (glemur_vjp_step) and print its line")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no comparisons, e2e or CPU baseline (profiling)")
+    ap.add_argument("--min-seconds", type=float, default=MIN_TIMED_S,
+                    help="repeat the block of timed steps until this much device time "
+                         "(0: time the block once, for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

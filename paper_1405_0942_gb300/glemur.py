@@ -421,33 +421,39 @@ def relax_with_schedule(relax, x0, n_steps):
     return dts
 
 
-def loss_and_field_gradient(relax, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
-    """Loss of the state reached from x0 by the step-size schedule `dts`
-    (replayed exactly: the control law is piecewise constant in the inputs)
-    and its gradient with respect to the relaxation's B0.
-
-    Memory: positions are kept every `checkpoint_every` steps; the backward
-    pass recomputes each segment forwards, storing its states, then runs the
-    steps' vector-Jacobian products in reverse (glemur_vjp_step).
-    """
-    import torch
-    n = len(dts)
+def forward_checkpoints(relax, x0, dts, checkpoint_every=50):
+    """Replay the step-size schedule `dts` from x0 (step_fixed), keeping the
+    exact raw state every `checkpoint_every` steps (and at step 0): the
+    forward half of the adjoint.  Leaves the relaxation at the final state."""
     every = max(1, int(checkpoint_every))
     relax.set_x(x0)
     ckpts = [relax.get_state()]
+    n = len(dts)
     for i, dt in enumerate(dts):
         relax.step_fixed(dt)
         if (i + 1) % every == 0 and i + 1 < n:
             ckpts.append(relax.get_state())
+    return ckpts
+
+
+def reverse_sweep(relax, ckpts, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+    """The backward half: from checkpoints of forward_checkpoints (same
+    `checkpoint_every`), recompute each segment forwards keeping its states,
+    seed the loss gradient at the final state and run the steps'
+    vector-Jacobian products in reverse (glemur_vjp_step).  Returns (loss
+    value, dL/dB0, dL/dx0)."""
+    import torch
+    n = len(dts)
+    every = max(1, int(checkpoint_every))
     lam = torch.zeros(relax.shape, dtype=torch.float64, device=relax.device)
     lam_next = torch.zeros_like(lam)
     mu = torch.zeros_like(lam)
-    value = None
-    nseg = (n + every - 1) // every if n > 0 else 0
     if n == 0:
-        relax.set_x(x0)
-        value = relax.loss_grad(loss, lam, mu)
-        return value, mu, lam
+        relax.set_state(ckpts[0])
+        value = relax.loss_grad(loss, lam_next, mu)
+        return value, mu, lam_next
+    value = None
+    nseg = (n + every - 1) // every
     for c in reversed(range(nseg)):
         start, end = c * every, min((c + 1) * every, n)
         relax.set_state(ckpts[c])
@@ -466,9 +472,68 @@ def loss_and_field_gradient(relax, x0, dts, loss=LOSS_ENERGY, checkpoint_every=5
     return value, mu, lam_next
 
 
+def loss_and_field_gradient(relax, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+    """Loss of the state reached from x0 by the step-size schedule `dts`
+    (replayed exactly: the control law is piecewise constant in the inputs)
+    and its gradient with respect to the relaxation's B0 (and to x0).
+
+    Memory: positions are kept every `checkpoint_every` steps; the backward
+    pass recomputes each segment forwards, storing its states, then runs the
+    steps' vector-Jacobian products in reverse (glemur_vjp_step).
+    """
+    ckpts = forward_checkpoints(relax, x0, dts, checkpoint_every)
+    return reverse_sweep(relax, ckpts, dts, loss, checkpoint_every)
+
+
+def _loss_value(relax, loss):
+    if loss == LOSS_ENERGY:
+        return relax.energy()
+    return relax.forcefree_err()[0]
+
+
 class RelaxationLoss:
-    """torch.autograd.Function factory: loss(B0) of the relaxed state, with
-    the hand-written adjoint as its backward."""
+    """torch.autograd.Function of the initial-field parameters theta: the
+    loss (final E_M or xi) of the state reached from x0 by the frozen
+    step-size schedule `dts`, for B0 = field(theta).
+
+    `field(theta)` returns (B0, dB0) as CUDA float64 tensors: B0 of shape
+    (3, nz, ny, nx) and its parameter derivatives dB0 of shape
+    (P, 3, nz, ny, nx).  forward() only relaxes (checkpointing the state
+    every `checkpoint_every` steps) and returns the loss; backward() runs the
+    reverse sweep from the checkpoints and contracts the field adjoint with
+    dB0 on the device (glemur_param_contract)."""
+
+    @staticmethod
+    def apply(relax, theta, field, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, th):
+                B0, dB0 = field(th.detach())
+                relax.set_B0(B0)
+                ckpts = forward_checkpoints(relax, x0, dts, checkpoint_every)
+                value = _loss_value(relax, loss)
+                ctx.ckpts = ckpts
+                ctx.dB0 = dB0
+                ctx.B0 = B0
+                return torch.tensor(value, dtype=torch.float64, device=th.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                relax.set_B0(ctx.B0)
+                _, mu, _ = reverse_sweep(relax, ctx.ckpts, dts, loss, checkpoint_every)
+                grad = param_contract(ctx.dB0, mu)
+                ctx.ckpts = ctx.dB0 = ctx.B0 = None
+                return g * grad.to(g.device)
+
+        return _Fn.apply(theta)
+
+
+class RelaxationFieldLoss:
+    """torch.autograd.Function of the nodal initial field B0 itself: the
+    same loss, gradient dL/dB0 (forward relaxes and checkpoints, backward
+    runs the reverse sweep)."""
 
     @staticmethod
     def apply(relax, B0, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
@@ -478,13 +543,16 @@ class RelaxationLoss:
             @staticmethod
             def forward(ctx, B0_):
                 relax.set_B0(B0_.detach())
-                value, mu, _ = loss_and_field_gradient(relax, x0, dts, loss, checkpoint_every)
-                ctx.save_for_backward(mu)
-                return torch.tensor(value, dtype=torch.float64, device=B0_.device)
+                ctx.ckpts = forward_checkpoints(relax, x0, dts, checkpoint_every)
+                ctx.B0 = B0_.detach()
+                return torch.tensor(_loss_value(relax, loss), dtype=torch.float64,
+                                    device=B0_.device)
 
             @staticmethod
             def backward(ctx, g):
-                (mu,) = ctx.saved_tensors
+                relax.set_B0(ctx.B0)
+                _, mu, _ = reverse_sweep(relax, ctx.ckpts, dts, loss, checkpoint_every)
+                ctx.ckpts = ctx.B0 = None
                 return g * mu
 
         return _Fn.apply(B0)

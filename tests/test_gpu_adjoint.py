@@ -145,15 +145,53 @@ def test_parameter_gradient_through_steps(G, loss):
 
 
 def test_autograd_function(G):
-    """torch.autograd through RelaxationLoss gives the field gradient."""
+    """torch.autograd through RelaxationFieldLoss gives the field gradient."""
     g, X, x0, regs = case(10, 10, 10)
     B0 = cuda(gi.braid_field(X, regs)).requires_grad_(True)
     r = G.Relaxation(g.nx, g.ny, g.nz)
     dts = [2e-3] * 4
-    L = G.RelaxationLoss.apply(r, B0, cuda(x0), dts, 0, 2)
+    L = G.RelaxationFieldLoss.apply(r, B0, cuda(x0), dts, 0, 2)
     L.backward()
     _, mu, _ = G.loss_and_field_gradient(r, cuda(x0), dts, 0, checkpoint_every=3)
     assert torch.allclose(B0.grad, mu, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("loss", [0, 1], ids=["energy", "xi"])
+def test_autograd_over_parameters(G, loss):
+    """RelaxationLoss is an autograd.Function of theta (the 6 amplitudes and
+    6 widths): forward only relaxes and checkpoints (no reverse step runs),
+    returns the loss of the final state; backward runs the reverse sweep and
+    contracts with dB0/dtheta on the device -- the same gradient as the
+    explicit adjoint and contraction."""
+    g, X, x0, regs = case(12, 11, 13)
+    m = len(regs)
+    r = G.Relaxation(g.nx, g.ny, g.nz)
+    dts = [2e-3] * 7
+
+    def field(th):
+        t = th.cpu().numpy()
+        rg = [(rr[0], rr[1], rr[2], t[i], t[m + i], rr[5]) for i, rr in enumerate(regs)]
+        return cuda(gi.braid_field(X, rg)), cuda(gi.braid_field_param_grad(X, rg))
+
+    theta = torch.tensor([rr[3] for rr in regs] + [rr[4] for rr in regs], dtype=torch.float64,
+                         device="cuda", requires_grad=True)
+    calls = []
+    orig = r.vjp_step
+    r.vjp_step = lambda *a: (calls.append(1), orig(*a))[1]
+    L = G.RelaxationLoss.apply(r, theta, field, cuda(x0), dts, loss, 3)
+    assert not calls                                  # forward: no reverse work
+    r.set_x(cuda(x0))
+    for dt in dts:
+        r.step_fixed(dt)
+    ref_val = r.energy() if loss == 0 else r.forcefree_err()[0]
+    assert float(L) == pytest.approx(ref_val, rel=1e-14)
+    (2.0 * L).backward()
+    assert len(calls) == len(dts)
+    B0, dB = field(theta.detach())
+    r.set_B0(B0)
+    value, mu, _ = G.loss_and_field_gradient(r, cuda(x0), dts, loss, checkpoint_every=3)
+    want = 2.0 * G.param_contract(dB, mu)
+    assert torch.allclose(theta.grad, want, rtol=1e-12, atol=0)
 
 
 def test_adjoint_96_cubed_500_steps_vs_fd(G):
@@ -188,3 +226,83 @@ def test_adjoint_96_cubed_500_steps_vs_fd(G):
             vals.append(r.energy())
         d_fd = (vals[0] - vals[1]) / (2 * hh)
         assert abs(grad[p] - d_fd) < 1e-6 * max(abs(grad[p]), 1e-7 * value), (p, grad[p], d_fd)
+
+
+def _argmax_xi(G, r, g, B0):
+    """Interior node of max |J x B| / B^2 of the relaxation's state: u = J x B
+    from the library, B the oracle's pull-back of B0 on the same positions."""
+    u = r.velocity().cpu().numpy()
+    x = r.get_x().cpu().numpy()
+    B, _, _ = ora.pullback(g, x, B0)
+    q = np.sqrt((u * u).sum(0)) / (B * B).sum(0)
+    q[[0, -1], :, :] = 0
+    q[:, [0, -1], :] = 0
+    q[:, :, [0, -1]] = 0
+    return np.unravel_index(np.argmax(q), q.shape)
+
+
+def test_adjoint_96_cubed_500_steps_xi_vs_fd(G):
+    """The 96^3 braid, 500 error-controlled steps (schedule frozen),
+    checkpoints every 50: gradient of the final force-free error xi (taken at
+    its argmax node) with respect to the 12 parameters against central
+    differences, h = 1e-4 relative.  xi is a maximum: its difference
+    quotient is the derivative only while the argmax node stays put, so the
+    node is checked at theta and at both theta +- h."""
+    w = gi.make_workload("adjoint")
+    g = w.grid
+    X = gi.nodes(g)
+    r = relax_for(G, g, w.x0, w.B0)
+    x0 = cuda(w.x0)
+    dts = G.relax_with_schedule(r, x0, 500)
+    value, mu, _ = G.loss_and_field_gradient(r, x0, dts, 1, checkpoint_every=50)
+    grad = G.param_contract(cuda(gi.braid_field_param_grad(X, w.regions)), mu).cpu().numpy()
+    r.set_x(x0)
+    for dt in dts:
+        r.step_fixed(dt)
+    node0 = _argmax_xi(G, r, g, w.B0)
+    theta = np.array(w.theta)
+    m = len(w.regions)
+    for p in range(len(theta)):
+        hh = 1e-4 * abs(theta[p])
+        vals = []
+        for sgn in (1, -1):
+            th = theta.copy()
+            th[p] += sgn * hh
+            regs = [(rr[0], rr[1], rr[2], th[i], th[m + i], rr[5]) for i, rr in enumerate(w.regions)]
+            B0p = gi.braid_field(X, regs)
+            r.set_B0(cuda(B0p))
+            r.set_x(x0)
+            for dt in dts:
+                r.step_fixed(dt)
+            vals.append(r.forcefree_err()[0])
+            assert _argmax_xi(G, r, g, B0p) == node0, (p, sgn)
+        d_fd = (vals[0] - vals[1]) / (2 * hh)
+        assert abs(grad[p] - d_fd) < 1e-6 * max(abs(grad[p]), 1e-7 * value), (p, grad[p], d_fd)
+    r.set_B0(cuda(w.B0))
+
+
+def test_adjoint_96_cubed_vs_complex_step_oracle(G):
+    """At 96^3 over the first 20 steps of the error-controlled schedule: the
+    GPU parameter gradient of both losses, dotted with a random direction in
+    theta, against the complex-step derivative of the FP64 oracle along that
+    direction (exact to rounding), within 1e-8."""
+    import multiprocessing as mp
+    w = gi.make_workload("adjoint")
+    g = w.grid
+    X = gi.nodes(g)
+    r = relax_for(G, g, w.x0, w.B0)
+    x0 = cuda(w.x0)
+    dts = G.relax_with_schedule(r, x0, 20)
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(12)
+    jobs = [(96, list(dts), v, loss, H) for loss in (0, 1)]
+    from oracle_jobs import cs_braid_direction
+    with mp.get_context("spawn").Pool(2) as pool:
+        res = pool.map(cs_braid_direction, jobs)
+    dB = cuda(gi.braid_field_param_grad(X, w.regions))
+    for loss, (Lr, dL, rc) in zip((0, 1), res):
+        assert rc == ora.OK
+        value, mu, _ = G.loss_and_field_gradient(r, x0, dts, loss, checkpoint_every=50)
+        assert abs(value - Lr) < 1e-12 * abs(Lr)
+        grad = G.param_contract(dB, mu).cpu().numpy()
+        assert abs(grad @ v - dL) < 1e-8 * abs(dL), (loss, grad @ v, dL)
