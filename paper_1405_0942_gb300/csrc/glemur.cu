@@ -405,7 +405,7 @@ Layout layout(int nx, int ny, int nz, int precision) {
   // two-pass stages
   L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
                                                           align256((size_t)N * 8) +
-                                                          align256((size_t)(9 * N) * 8)
+                                                          align256((size_t)(10 * N) * 8)
                                                     : 0);
   L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.split;
   return L;
@@ -503,7 +503,7 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.ys[0] = (double*)c->ys[0];
   a.ys[1] = (double*)c->ys[1];
   a.Bb = c->Bb;
-  a.rb = c->rb;
+  a.rb = nullptr;  // pass C reads 1/det G with the differences in Gb
   a.Gb = c->Gb;
   a.diag = diag;
   a.force = force;

@@ -157,10 +157,11 @@ struct SplitArgs {
   double* ys[2];       // stage inputs: y_s in ys[s & 1] (s >= 1), 3N each;
                        // boundary entries hold the fixed boundary positions
   double* Bb;          // B, 3N
-  double* rb;          // 1/det G, N
-  double* Gb;          // index-space differences g_0, g_1, g_2 at every
-                       // interior node, 9N: component c of g_a at
-                       // Gb[(3a + c) N + n] (written by pass B, read by C)
+  double* rb;          // 1/det G, N, or null (then written to Gb only)
+  double* Gb;          // per interior node n, 10 doubles at Gb + 10 n
+                       // (16-byte aligned): g_0, g_1, g_2 (index-space
+                       // differences, 3 components each) and 1/det G --
+                       // written by pass B, read by pass C
   int diag, force;
   int periodic;        // periodic in z: planes 0, nz-1 are ghosts of nz-2, 1
   DevState* st;

@@ -17,10 +17,11 @@
 //            k_s and, pointwise, the next stage input
 //            y_{s+1} = d + sum_{j<=s} dt a_{s+1,j} k_j; the last stage
 //            writes the fifth-order update and the embedded error instead.
-// Pass C reads g_a as pass B stored it rather than forming it again from
-// the stage input's neighbours: 12 fewer FP64 additions per interior node
-// and stage for 72 more bytes written and read, which HBM (used at well
-// under a fifth of its bandwidth by these passes) absorbs.
+// Pass C reads g_a (and 1/det G) as pass B stored them, interleaved per
+// node, rather than forming g_a again from the stage input's neighbours:
+// 12 fewer FP64 additions per interior node and stage for 80 bytes written
+// and read (five 16-byte accesses each way), which HBM (used at well under
+// a fifth of its bandwidth by these passes) absorbs.
 // Each pass runs one wave of CTAs (as many as fit on the SMs: each pass
 // sizes its own grid), each over a contiguous range of whole warps of
 // nodes: the FP64 pipe is per SM, so every SM gets the same number of
@@ -129,18 +130,21 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
     g0[0] += a.h2[0];
     g1[1] += a.h2[1];
     g2[2] += a.h2[2];
-    // 9N may exceed the 32-bit range the 3N fields stay within
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      a.Gb[(size_t)c * N + n] = g0[c];
-      a.Gb[(size_t)(3 + c) * N + n] = g1[c];
-      a.Gb[(size_t)(6 + c) * N + n] = g2[c];
-    }
   }
   const double det = det3(g0, g1, g2);
   if (le_zero(det))  // NaN: reported by the error norm
     atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   const double r = recip(det);
+  if (!FACE) {
+    // the node's differences and 1/det G for pass C, as five 16-byte
+    // stores (10 N doubles: size_t offsets)
+    double2* q = reinterpret_cast<double2*>(a.Gb + (size_t)n * 10);
+    q[0] = make_double2(g0[0], g0[1]);
+    q[1] = make_double2(g0[2], g1[0]);
+    q[2] = make_double2(g1[1], g1[2]);
+    q[3] = make_double2(g2[0], g2[1]);
+    q[4] = make_double2(g2[2], r);
+  }
   const double b0 = __ldg(&a.B0s[n]), b1 = __ldg(&a.B0s[N + n]), b2 = __ldg(&a.B0s[2 * N + n]);
   double B[3];
 #pragma unroll
@@ -148,7 +152,7 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
     B[c] = (g0[c] * b0 + g1[c] * b1 + g2[c] * b2) * r;
     a.Bb[c * N + nw] = B[c];
   }
-  a.rb[nw] = r;
+  if (a.rb) a.rb[nw] = r;
   if (!energy) return 0.0;
   // eq. "magnetic energy": zeta halves per boundary index coordinate
   const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) + (k == 0 || k == a.nz - 1);
@@ -350,12 +354,16 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
       nnn_current(a, S == 0 ? d : a.ys[S & 1], N, n, J, B);
     } else {
       double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
+      const double2* q = reinterpret_cast<const double2*>(a.Gb + (size_t)n * 10);
+      const double2 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3),
+                    q4 = __ldg(q + 4);
+      g0[0] = q0.x; g0[1] = q0.y; g0[2] = q1.x;
+      g1[0] = q1.y; g1[1] = q2.x; g1[2] = q2.y;
+      g2[0] = q3.x; g2[1] = q3.y; g2[2] = q4.x;
+      const double r = q4.y;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double* b = a.Bb + c * N;
-        g0[c] = __ldg(&a.Gb[(size_t)c * N + n]);
-        g1[c] = __ldg(&a.Gb[(size_t)(3 + c) * N + n]);
-        g2[c] = __ldg(&a.Gb[(size_t)(6 + c) * N + n]);
         P0[c] = __ldg(&b[n + 1]) - __ldg(&b[n - 1]);
         P1[c] = __ldg(&b[n + sy]) - __ldg(&b[n - sy]);
         P2[c] = __ldg(&b[n + sz]) - __ldg(&b[n - sz]);
@@ -364,7 +372,6 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
       const double c0 = dot3_sub(P1, g2, P2, g1);
       const double c1 = dot3_sub(P2, g0, P0, g2);
       const double c2 = dot3_sub(P0, g1, P1, g0);
-      const double r = __ldg(&a.rb[n]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) J[c] = (c0 * g0[c] + c1 * g1[c] + c2 * g2[c]) * r;
     }

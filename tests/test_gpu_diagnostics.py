@@ -137,8 +137,8 @@ def _isohelix_run(G, n, curl, table):
 def test_isohelix_table1(G):
     """Table 1 (IsoHelix, phi = pi/4, double precision) on the GPU at
     n = 17, 33, 65.  Mimetic: the printed epsilon*, sigma_B and sigma_x to
-    within 10 % at n = 17 and 33, within a factor of two at n = 65, each
-    falling with n as the table's do.  Classic (this library's reading of a
+    within 10 % at every n (measured: within 5 %), each falling with n as
+    the table's do.  Classic (this library's reading of a
     formula the paper does not print): the paper's central comparison --
     epsilon* more than ten times and sigma_B more than three times the
     mimetic value at every n.  (The paper's classic epsilon* stays of order
@@ -155,13 +155,11 @@ def test_isohelix_table1(G):
     print({f"{k[0]}{k[1]}": {kk: float(f"{vv:.3g}") for kk, vv in v.items()}
            for k, v in res.items()})
     keys = ("eps_star", "sigma_B", "sigma_x")
-    for n, rel in ((17, 0.1), (33, 0.1)):
+    for n in (17, 33, 65):
         for key in keys:
             assert res[("mimetic", n)][key] == pytest.approx(table["mimetic"][str(n)][key],
-                                                             rel=rel), (n, key)
+                                                             rel=0.1), (n, key)
     for key in keys:
-        ref = table["mimetic"]["65"][key]
-        assert 0.5 * ref < res[("mimetic", 65)][key] < 2.0 * ref, key
         assert res[("mimetic", 65)][key] < res[("mimetic", 33)][key] \
             < res[("mimetic", 17)][key], key
     for n in (17, 33, 65):

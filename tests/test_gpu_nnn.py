@@ -69,7 +69,9 @@ def test_one_step_nnn(G, dims):
     x = r.get_x().cpu().numpy()
     assert rel_inf(x, x_ref) < 1e-12
     assert np.abs(x - x_ref).max() < 1e-9 * np.abs(x_ref - x0).max()
-    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref
+    # Lambda is a cancelling sum dt sum_j (b_j - b*_j) k_j: besides 1e-9 of
+    # itself it carries absolute rounding ~ eps |dt k| ~ eps |step|
+    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref + 1e-15 * np.abs(x_ref - x0).max()
 
 
 def test_diagnostics_nnn(G):
