@@ -158,6 +158,14 @@ size_t glemur_workspace_bytes(int nx, int ny, int nz, int precision);
  *                         recomputation) instead of the two-pass stages
  *   GLEMUR_KZ=k           z-planes per CTA of the stage kernels instead of
  *                         the cost model's choice
+ *   GLEMUR_PERSIST=0      FP64 two-pass stages: one launch per pass and one
+ *                         for the control instead of whole attempts in one
+ *                         persistent cooperative launch (line-tied contexts;
+ *                         periodic contexts always use the per-pass kernels)
+ *   GLEMUR_TEST_PERSIST_TIMEOUT=1  test hook: in the persistent launch one
+ *                         CTA never reports a finished pass, so the bounded
+ *                         waits of its neighbours give up after 2 s and
+ *                         steps fail with GLEMUR_ERR_TIMEOUT
  *   GLEMUR_TEST_TMA_TIMEOUT=1 or 2  test hook: the TMA stage kernels' first
  *                         tile wait (1) or first wait inside their plane loop
  *                         (2, CTAs of at least two z-planes) also waits on a

@@ -11,6 +11,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "control.cuh"
 #include "glemur.h"
 #include "glemur_dev.cuh"
 #include "tma.cuh"
@@ -36,21 +37,9 @@ int tile_rows_f32_mimetic_tma();
 
 cudaError_t launch_f64_split(const SplitArgs& a, int stage, cudaStream_t s, int curl);
 void split_ctas_per_sm(int b[6], int c[6], int curl);
-
-// Cash-Karp embedded 5(4) pair (Cash & Karp, ACM TOMS 16, 1990), the scheme
-// of section "Time Stepping".
-__constant__ double CK_A[6][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5.0, 0, 0, 0, 0, 0},
-    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
-    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0, 0},
-    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0, 0},
-    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0,
-     253.0 / 4096.0, 0}};
-__constant__ double CK_B5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0,
-                                512.0 / 1771.0};
-__constant__ double CK_B4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0,
-                                13525.0 / 55296.0, 277.0 / 14336.0, 1.0 / 4.0};
+int persist_ctas_per_sm(int curl);
+cudaError_t launch_f64_persist(const SplitArgs& a, const PersistArgs& pa, int grid, int curl,
+                               cudaStream_t s);
 
 // dt-scaled coefficients of the pending attempt.
 __device__ void set_coeffs(DevState* st) {
@@ -103,81 +92,12 @@ __global__ void k_set_dt(DevState* st, double dt, int replay) {
   set_coeffs(st);
 }
 
-// Sum and max reductions of the per-CTA diagnostic partials (fixed order).
-__device__ void finalize_diag(DevState* st, const double* part, int nb, double* sh) {
-  double e = 0.0, x2 = 0.0, xs2 = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    e += part[PART_E * nb + b];
-    x2 = nanmax(x2, part[PART_XI2 * nb + b]);
-    xs2 = nanmax(xs2, part[PART_XIS2 * nb + b]);
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    x2 = nanmax(x2, __shfl_xor_sync(0xffffffffu, x2, o));
-    xs2 = nanmax(xs2, __shfl_xor_sync(0xffffffffu, xs2, o));
-  }
-  __syncthreads();
-  if (lane == 0) {
-    sh[w] = e;
-    sh[32 + w] = x2;
-    sh[64 + w] = xs2;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double E = 0.0, X = 0.0, XS = 0.0;
-    for (int i = 0; i < nw; ++i) {
-      E += sh[i];
-      X = nanmax(X, sh[32 + i]);
-      XS = nanmax(XS, sh[64 + i]);
-    }
-    st->E = E / 16.0;  // eq. "magnetic energy" in index-space units
-    st->xi = sqrt(X);
-    st->xi_sin = sqrt(XS);
-  }
-}
-
 __global__ void k_diag_finalize(DevState* st, const double* part, int nb) {
   __shared__ double sh[96];
-  finalize_diag(st, part, nb, sh);
+  finalize_diag<LdPlain>(st, part, nb, sh);
   if (threadIdx.x == 0 && (st->flags & FLAG_TIMEOUT)) st->status = ST_TIMEOUT;
 }
 
-// r^0.2 for the step-size law of eq. "time stepping": one Newton step on
-// y^5 = r (Newton's method for the n-th root, y <- ((n-1) y + r / y^(n-1))
-// / n, which converges quadratically) from an FP32 estimate: ~1e-7 -> ~1e-14
-// relative, with a handful of FP64 operations instead of a double pow on
-// GB300's narrow FP64 pipe.  Outside the estimate's float range, pow.
-__device__ double fifth_root(double r) {
-  if (!(r > 1e-30 && r < 1e30)) return pow(r, 0.2);
-  const double y = (double)powf((float)r, 0.2f);
-  const double y2 = y * y;
-  return 0.2 * (4.0 * y + r / (y2 * y2));
-}
-
-// dt-scaled coefficients for step size dt, one entry per thread (the 36
-// a_sj and the 6 b_j, b_j - b*_j; threads >= 42 idle).
-__device__ void set_coeffs_parallel(DevState* st, double dt) {
-  const int t = threadIdx.x;
-  if (t < 36) {
-    const int s = t / 6, j = t % 6;
-    const double v = dt * CK_A[s][j];
-    st->dta[s][j] = v;
-    st->dtaf[s][j] = (float)v;
-  } else if (t < 42) {
-    const int s = t - 36;
-    const double b = dt * CK_B5[s], e = dt * (CK_B5[s] - CK_B4[s]);
-    st->dtb[s] = b;
-    st->dte[s] = e;
-    st->dtbf[s] = (float)b;
-    st->dtef[s] = (float)e;
-  }
-}
-
-// Eq. "time stepping" and the acceptance rule around it, after each attempt.
-// Thread 0 takes the decision from a snapshot of the control state (all
-// loads independent, then all stores); the block then writes the dt-scaled
-// coefficients of the next attempt in parallel.
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = getenv("GLEMUR_PDL");
@@ -186,94 +106,13 @@ bool pdl_enabled() {
   return on;
 }
 
+// Eq. "time stepping" and the acceptance rule after each attempt (see
+// control.cuh), as a kernel of one CTA.
 __global__ void k_control(DevState* st, const double* part, int nb, int diag, double* dtlog) {
   pdl_trigger();
   pdl_wait();
-  if (st->status != ST_OK || st->n_accept >= st->target) return;
   __shared__ double sh[96];
-  __shared__ double dt_next;
-  __shared__ int go_on;
-  double m = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = nanmax(m, part[PART_LAMBDA * nb + b]);
-  for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = nanmax(m, sh[i]);
-    sh[95] = m;
-  }
-  __syncthreads();
-  if (diag) finalize_diag(st, part, nb, sh);
-  if (threadIdx.x == 0) {
-    const double lam = sh[95];
-    const double dt = st->dt, lambda0 = st->lambda0, safety = st->safety;
-    const double shrink_min = st->shrink_min, grow_max = st->grow_max, dt_min = st->dt_min;
-    const double t = st->t;
-    const unsigned flags = st->flags;
-    const int replay = st->replay, consec = st->consec, max_rejects = st->max_rejects;
-    const int cur = st->cur;
-    const long long n_acc = st->n_accept, n_rej = st->n_reject;
-    int status = ST_OK;
-    bool accept = false;
-    double dtn = dt;
-    const bool folded = (flags & FLAG_FOLDED_TRIAL) != 0;
-    double lam_out = lam;
-    if (flags & FLAG_TIMEOUT) {
-      status = ST_TIMEOUT;
-    } else if (flags & FLAG_COLLAPSED) {
-      status = ST_COLLAPSED;
-    } else if (!folded && !isfinite(lam)) {
-      status = ST_NONFINITE;
-    } else if (folded) {
-      // a trial stage folded the grid: reject with the largest shrink
-      dtn = dt * shrink_min;
-      lam_out = INFINITY;
-      if (consec + 1 > max_rejects || dtn < dt_min) status = ST_DT_UNDERFLOW;
-    } else if (replay) {
-      accept = true;
-    } else if (lam > lambda0) {
-      double fac = safety * fifth_root(lambda0 / lam);
-      if (fac < shrink_min) fac = shrink_min;
-      dtn = dt * fac;
-      if (consec + 1 > max_rejects || dtn < dt_min) status = ST_DT_UNDERFLOW;
-    } else {
-      accept = true;
-      double fac = 1.0;
-      if (lam < 0.5 * lambda0) {
-        fac = lam > 0.0 ? safety * fifth_root(lambda0 / lam) : grow_max;
-        if (fac > grow_max) fac = grow_max;
-      }
-      dtn = dt * fac;
-    }
-    st->lambda = lam_out;
-    if (status != ST_OK) {
-      // the attempt ends the run: counted as a rejection, state untouched
-      st->status = status;
-      st->n_reject = n_rej + 1;
-      if (status == ST_DT_UNDERFLOW) st->consec = consec + 1;
-      go_on = 0;
-    } else {
-      if (replay) st->replay = 0;
-      if (accept) {
-        // the step-size log: accepted step n_acc in slot n_acc mod the ring
-        dtlog[n_acc % GLEMUR_DT_LOG] = dt;
-        st->dt_last = dt;
-        st->t = t + dt;
-        st->cur = cur ^ 1;
-        st->n_accept = n_acc + 1;
-        st->consec = 0;
-      } else {
-        st->n_reject = n_rej + 1;
-        st->consec = consec + 1;
-      }
-      st->dt = dtn;
-      st->flags = 0;
-      dt_next = dtn;
-      go_on = 1;
-    }
-  }
-  __syncthreads();
-  if (go_on) set_coeffs_parallel(st, dt_next);
+  control_block<LdPlain>(st, part, nb, diag, dtlog, sh);
 }
 
 // ---- layout conversions at the boundary (float64 SoA fields) ----------
@@ -370,6 +209,11 @@ struct glemur_ctx {
   double* Gb;                            // split path: g_0, g_1, g_2
   int max_blocks, nblocks, kz;          // mimetic-current launches
   int split_grid_b[6] = {}, split_grid_c[6] = {};  // FP64 two-pass grids (CTAs)
+  int persist;                           // whole attempts in one persistent launch
+  int persist_grid;                      // its CTAs (all resident)
+  PersistArgs pa;                        // its plan and counters (workspace)
+  int* persist_base;                     // counters to zero before each launch
+  size_t persist_zero_bytes;
   int nblocks_direct, kz_direct;         // direct-current launches
   dim3 grid, grid_direct;
   int nsm;
@@ -379,8 +223,10 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+constexpr int PERSIST_MAX_CTAS = 16384;
+
 struct Layout {
-  size_t field, stage, part, state, ptrs, dtlog, split, total;
+  size_t field, stage, part, state, ptrs, dtlog, persist, split, total;
   int max_blocks;
 };
 
@@ -401,17 +247,120 @@ Layout layout(int nx, int ny, int nz, int precision) {
   L.state = align256(sizeof(DevState));
   L.ptrs = 256;
   L.dtlog = align256((size_t)GLEMUR_DT_LOG * sizeof(double));
+  // persistent FP64 attempts: counters and touches per plane (4 nz ints),
+  // the barrier, and the plan of up to PERSIST_MAX_CTAS CTAs
+  L.persist = precision == GLEMUR_FP64
+                  ? align256(sizeof(int) * (4 * (size_t)nz + 64 +
+                                            (size_t)PERSIST_MAX_CTAS * (2 * PERSIST_BI + 2)))
+                  : 0;
   // two stage inputs (mimetic stages); FP64 also B and 1/det G for the
   // two-pass stages
   L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
                                                           align256((size_t)N * 8) +
                                                           align256((size_t)(10 * N) * 8)
                                                     : 0);
-  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.split;
+  L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.persist + L.split;
   return L;
 }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA; }
+
+// Node range [begin, end) of CTA b of G over n items in whole warps, as the
+// two-pass kernels' cta_range computes it on the device.
+void host_cta_range(long long n, int b, int G, long long& begin, long long& end) {
+  const long long W = (n + 31) / 32;
+  const long long w0 = W * b / G, w1 = W * (b + 1) / G;
+  begin = w0 * 32;
+  end = w1 * 32 < n ? w1 * 32 : n;
+}
+
+// Plane of boundary item t, in the order of the kernels' boundary_node:
+// the z faces (whole planes), the y faces without their z edges, the x
+// faces without their y and z edges.
+int host_boundary_plane(int nx, int ny, int nz, long long t) {
+  const long long fz = (long long)nx * ny, fy = (long long)nx * (nz - 2),
+                  fx = (long long)(ny - 2) * (nz - 2);
+  if (t < fz) return 0;
+  if (t < 2 * fz) return nz - 1;
+  t -= 2 * fz;
+  if (t < 2 * fy) return 1 + (int)((t < fy ? t : t - fy) / nx);
+  t -= 2 * fy;
+  return 1 + (int)((t < fx ? t : t - fx) / (ny - 2));
+}
+
+// The persistent kernel's plan: per CTA the plane intervals of its pass-B
+// work (interior range, then the boundary range split at the face blocks)
+// and of its pass-C work (the interior range); per plane how many CTAs'
+// intervals contain it.  False if the plan does not fit.
+bool persist_plan(glemur_ctx* c, int G) {
+  const int nx = c->nx, ny = c->ny, nz = c->nz;
+  if (G < 1 || G > PERSIST_MAX_CTAS) return false;
+  const long long N = c->N, NI = (long long)(nx - 2) * (ny - 2) * (nz - 2);
+  const long long A = (long long)(nx - 2) * (ny - 2);
+  const long long fz = (long long)nx * ny, fy = (long long)nx * (nz - 2),
+                  fx = (long long)(ny - 2) * (nz - 2);
+  const long long blk[7] = {0, fz, 2 * fz, 2 * fz + fy, 2 * fz + 2 * fy, 2 * fz + 2 * fy + fx,
+                            2 * fz + 2 * fy + 2 * fx};
+  int* h = new (std::nothrow) int[4 * (size_t)nz + 64 + (size_t)G * (2 * PERSIST_BI + 2)];
+  if (!h) return false;
+  int* cnt = h;                 // cntB, cntC: zeroed per launch
+  int* touchB = h + 2 * nz;
+  int* touchC = h + 3 * nz;
+  int* ivB = h + 4 * nz + 64;
+  int* ivC = ivB + (size_t)G * 2 * PERSIST_BI;
+  for (int i = 0; i < 4 * nz + 64; ++i) h[i] = 0;
+  (void)cnt;
+  for (int b = 0; b < G; ++b) {
+    int* vb = ivB + (size_t)b * 2 * PERSIST_BI;
+    for (int q = 0; q < PERSIST_BI; ++q) {
+      vb[2 * q] = 1;
+      vb[2 * q + 1] = 0;  // empty
+    }
+    long long t0, t1;
+    host_cta_range(NI, b, G, t0, t1);
+    int* vc = ivC + 2 * b;
+    vc[0] = 1;
+    vc[1] = 0;
+    if (t1 > t0) {
+      vc[0] = vb[0] = 1 + (int)(t0 / A);
+      vc[1] = vb[1] = 1 + (int)((t1 - 1) / A);
+    }
+    host_cta_range(N - NI, b, G, t0, t1);
+    int q = 1;
+    for (int f = 0; f < 6 && q < PERSIST_BI; ++f) {
+      const long long u = t0 > blk[f] ? t0 : blk[f], v = t1 < blk[f + 1] ? t1 : blk[f + 1];
+      if (v <= u) continue;
+      vb[2 * q] = host_boundary_plane(nx, ny, nz, u);
+      vb[2 * q + 1] = host_boundary_plane(nx, ny, nz, v - 1);
+      ++q;
+    }
+    for (int qq = 0; qq < PERSIST_BI; ++qq)
+      for (int pl = vb[2 * qq]; pl <= vb[2 * qq + 1]; ++pl) ++touchB[pl];
+    for (int pl = vc[0]; pl <= vc[1]; ++pl) ++touchC[pl];
+  }
+  const size_t bytes = sizeof(int) * (4 * (size_t)nz + 64 + (size_t)G * (2 * PERSIST_BI + 2));
+  cudaError_t e = cudaMemcpyAsync(c->persist_base, h, bytes, cudaMemcpyHostToDevice, c->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+  delete[] h;
+  if (e != cudaSuccess) return false;
+  int* d = c->persist_base;
+  c->pa.cntB = d;
+  c->pa.cntC = d + nz;
+  c->pa.touchB = d + 2 * nz;
+  c->pa.touchC = d + 3 * nz;
+  c->pa.bar = (unsigned*)(d + 4 * nz);
+  c->pa.ivB = d + 4 * nz + 64;
+  c->pa.ivC = c->pa.ivB + (size_t)G * 2 * PERSIST_BI;
+  c->pa.dtlog = c->dtlog;
+  c->pa.n_attempts = 0;
+  // GLEMUR_TEST_PERSIST_TIMEOUT=1: one CTA withholds a pass's completion so
+  // that the bounded waits give up (the attempt ends with TIMEOUT, no fault)
+  const char* tp = getenv("GLEMUR_TEST_PERSIST_TIMEOUT");
+  c->pa.test_withhold = tp && atoi(tp) == 1 ? G / 2 : -1;
+  c->persist_grid = G;
+  c->persist_zero_bytes = sizeof(int) * (4 * (size_t)nz + 64);
+  return true;
+}
 
 GridGeom geom(const glemur_ctx* c) {
   GridGeom g;
@@ -545,6 +494,42 @@ cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int
   return launch_f64_mimetic(a, stage, g, c->s);
 }
 
+// n attempts in one persistent launch: the plane counters and the barrier
+// start from zero (the per-plane touch counts after them are kept).
+cudaError_t launch_attempts_persist(const glemur_ctx* c, int n) {
+  SplitArgs a;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  for (int i = 0; i < 3; ++i) a.h2[i] = 2.0 * c->h[i];
+  a.d[0] = (const double*)c->dbuf[0];
+  a.d[1] = (const double*)c->dbuf[1];
+  a.B0s = (const double*)c->B0s;
+  for (int j = 0; j < 5; ++j) a.k[j] = (double*)c->k[j];
+  a.k[5] = nullptr;
+  a.ys[0] = (double*)c->ys[0];
+  a.ys[1] = (double*)c->ys[1];
+  a.Bb = c->Bb;
+  a.rb = nullptr;
+  a.Gb = c->Gb;
+  a.diag = c->o.diag_each_attempt ? 1 : 0;
+  a.force = 0;
+  a.periodic = 0;
+  a.st = c->st;
+  a.part = c->part;
+  a.nblocks = c->nblocks;
+  for (int j = 0; j < 6; ++j) a.grid_b[j] = a.grid_c[j] = c->persist_grid;
+  PersistArgs pa = c->pa;
+  pa.n_attempts = n;
+  // counters (2 nz ints) and the barrier (at 4 nz ints) start at zero
+  cudaError_t e = cudaMemsetAsync(c->persist_base, 0, sizeof(int) * 2 * c->nz, c->s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->persist_base + 4 * c->nz, 0, sizeof(int) * 64, c->s);
+  if (e == cudaSuccess)
+    e = launch_f64_persist(a, pa, c->persist_grid, c->o.curl == GLEMUR_CURL_NNN ? 2 : 0, c->s);
+  return e;
+}
+
 cudaError_t launch_attempt(const glemur_ctx* c) {
   const int diag = c->o.diag_each_attempt ? 1 : 0;
   for (int s = 0; s < 6; ++s) {
@@ -553,6 +538,28 @@ cudaError_t launch_attempt(const glemur_ctx* c) {
   }
   return launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
                     nblocks_of(c, c->o.curl), diag, c->dtlog);
+}
+
+// n attempts: one persistent launch where the context uses it, else the
+// per-pass kernels attempt by attempt.
+cudaError_t launch_attempts(const glemur_ctx* c, long long n) {
+  if (n <= 0) return cudaSuccess;
+  if (c->persist) {
+    // counters reach touch x 6 x attempts (touch <= PERSIST_MAX_CTAS): at
+    // most 16384 attempts per launch keep them within 32 bits
+    while (n > 0) {
+      const int m = n > 16384 ? 16384 : (int)n;
+      cudaError_t e = launch_attempts_persist(c, m);
+      if (e != cudaSuccess) return e;
+      n -= m;
+    }
+    return cudaSuccess;
+  }
+  for (long long i = 0; i < n; ++i) {
+    cudaError_t e = launch_attempt(c);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int read_state(glemur_ctx* c, DevState* hs) {
@@ -867,6 +874,7 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->st = (DevState*)p; p += L.state;
   c->dbuf_dev = (void**)p; p += L.ptrs;
   c->dtlog = (double*)p; p += L.dtlog;
+  c->persist_base = (int*)p; p += L.persist;
   c->max_blocks = L.max_blocks;
   c->split = 0;
   c->ys[0] = c->ys[1] = c->Bb = c->rb = c->Gb = nullptr;
@@ -926,6 +934,21 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
       c->split_grid_c[s] = (int)(need < cc ? need : cc);
       c->nblocks = c->split_grid_b[s] > c->nblocks ? c->split_grid_b[s] : c->nblocks;
       c->nblocks = c->split_grid_c[s] > c->nblocks ? c->split_grid_c[s] : c->nblocks;
+    }
+  }
+  // whole attempts in one persistent launch (FP64 two-pass stages, line-tied)
+  c->persist = 0;
+  if (c->split && !o.periodic_z) {
+    const char* pe = getenv("GLEMUR_PERSIST");
+    if (!(pe && pe[0] == '0')) {
+      const int per = persist_ctas_per_sm(o.curl == GLEMUR_CURL_NNN ? 2 : 0);
+      long long G = (long long)per * c->nsm;
+      const long long need = (c->N + 255) / 256;
+      if (G > need) G = need;
+      if (per >= 1 && persist_plan(c, (int)G)) {
+        c->persist = 1;
+        if (c->nblocks < (int)G) c->nblocks = (int)G;
+      }
     }
   }
   c->kz_direct = choose_kz(nz, gx * gy, c->nsm, pd, !mixed);
@@ -1036,7 +1059,7 @@ int glemur_attempts(glemur_ctx* c, int n_attempts) {
   if (!c || n_attempts < 0) return GLEMUR_ERR_BADARG;
   k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
   cudaError_t e = cudaGetLastError();
-  for (int i = 0; i < n_attempts && e == cudaSuccess; ++i) e = launch_attempt(c);
+  if (e == cudaSuccess) e = launch_attempts(c, n_attempts);
   return cuda_rc(e);
 }
 
@@ -1054,8 +1077,7 @@ int glemur_step(glemur_ctx* c, int n_accept, glemur_stats* stats) {
   if ((rc = cuda_rc(cudaGetLastError()))) return rc;
   while (hs.n_accept < target) {
     const long long remaining = target - hs.n_accept;
-    for (long long i = 0; i < remaining; ++i)
-      if ((rc = cuda_rc(launch_attempt(c)))) return rc;
+    if ((rc = cuda_rc(launch_attempts(c, remaining)))) return rc;
     if ((rc = read_state(c, &hs))) return rc;
     if (hs.status != ST_OK) break;
   }
@@ -1074,7 +1096,7 @@ int glemur_step_fixed(glemur_ctx* c, double dt, glemur_stats* stats) {
   }
   k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 1);
   if ((rc = cuda_rc(cudaGetLastError()))) return rc;
-  if ((rc = cuda_rc(launch_attempt(c)))) return rc;
+  if ((rc = cuda_rc(launch_attempts(c, 1)))) return rc;
   if ((rc = read_state(c, &hs))) return rc;
   fill_stats(hs, c->o.curl, stats);
   return hs.status;
@@ -1143,7 +1165,9 @@ int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
 }
 
 int glemur_kernels_per_attempt(const glemur_ctx* c) {
-  return c ? (c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 13 : 7) : 0;
+  if (!c) return 0;
+  if (c->persist) return 1;
+  return c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 13 : 7;
 }
 
 int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {

@@ -171,6 +171,27 @@ struct SplitArgs {
   int grid_c[6];       // CTAs of pass C of each stage
 };
 
+// The persistent FP64 attempt kernel's plan and synchronisation state
+// (workspace memory): per node plane, completion counters of pass B and
+// pass C and how many CTAs contribute to each; per CTA, the plane
+// intervals its pass-B work touches (at most 6: interior planes and the
+// boundary face blocks) and its pass-C interval (interior planes); an
+// arrival counter and a release generation for the end of each attempt.
+constexpr int PERSIST_BI = 6;  // pass-B intervals per CTA
+struct PersistArgs {
+  int* cntB;            // [nz]
+  int* cntC;            // [nz]
+  const int* touchB;    // [nz] contributions per plane and pass-B phase
+  const int* touchC;    // [nz]
+  const int* ivB;       // [G][PERSIST_BI][2] (lo, hi) inclusive, lo > hi: empty
+  const int* ivC;       // [G][2]
+  unsigned* bar;        // [2] arrivals, released generation
+  double* dtlog;        // accepted step-size ring
+  int n_attempts;       // attempts this launch
+  int test_withhold;    // test hook: this CTA never publishes pass B of
+                        // stage 3, so waits on it give up (-1: off)
+};
+
 // What the on-demand diagnostics (diagnostics.cu) need of a context.
 struct DiagCtx {
   int nx, ny, nz;

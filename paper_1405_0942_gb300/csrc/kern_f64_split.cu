@@ -31,9 +31,27 @@
 // leaves and start as soon as it ends; a grid of exactly the CTAs the SMs
 // hold cannot crowd one SM when it is placed that way.  The per-CTA
 // partials (Lambda, E_M, xi) keep the fused kernel's layout.
+#include "control.cuh"
 #include "stage_kernels.cuh"
+#include "tma.cuh"
 
 namespace glemur {
+
+// How the passes load data that another CTA of the same launch may have
+// written: the per-pass kernels use the read-only path (__ldg) -- each pass
+// only reads what earlier launches wrote -- while the persistent attempt
+// kernel, whose CTAs read each other's results within one launch, loads
+// such data through L2 (__ldcg), which other SMs' writes reach.
+struct LdRO {
+  __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ double2 ld2(const double2* p) { return __ldg(p); }
+  __device__ static __forceinline__ int ldi(const int* p) { return *p; }
+};
+struct LdL2 {
+  __device__ static __forceinline__ double ld(const double* p) { return __ldcg(p); }
+  __device__ static __forceinline__ double2 ld2(const double2* p) { return __ldcg(p); }
+  __device__ static __forceinline__ int ldi(const int* p) { return __ldcg(p); }
+};
 
 // This CTA's node range: warps [W b / G, W (b+1) / G) of the W = N/32 node
 // warps (rounded up), as node indices [begin, end).
@@ -85,6 +103,7 @@ __device__ __forceinline__ int boundary_node(const SplitArgs& a, int b, int& i, 
 }
 
 // Column a of G at node (i, j, k) from the stage input y.
+template <class LD>
 __device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __restrict__ y, int N,
                                            int n, int ax, int idx, int ext, int stride,
                                            double out[3]) {
@@ -94,11 +113,11 @@ __device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __r
     const double* v = y + c * N;
     double d;
     if (kind == 0)
-      d = __ldg(&v[n + stride]) - __ldg(&v[n - stride]);
+      d = LD::ld(&v[n + stride]) - LD::ld(&v[n - stride]);
     else if (kind == 1)
-      d = (4.0 * __ldg(&v[n + stride]) - 3.0 * __ldg(&v[n])) - __ldg(&v[n + 2 * stride]);
+      d = (4.0 * LD::ld(&v[n + stride]) - 3.0 * LD::ld(&v[n])) - LD::ld(&v[n + 2 * stride]);
     else
-      d = (3.0 * __ldg(&v[n]) - 4.0 * __ldg(&v[n - stride])) + __ldg(&v[n - 2 * stride]);
+      d = (3.0 * LD::ld(&v[n]) - 4.0 * LD::ld(&v[n - stride])) + LD::ld(&v[n - 2 * stride]);
     out[c] = d;
   }
   out[ax] += a.h2[ax];
@@ -109,23 +128,23 @@ __device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __r
 // that carries n's B); returns the node's energy term zeta |B|^2 det G if
 // `energy`.  FACE: the general stencil (one-sided differences on the
 // boundary faces the node touches), else central differences only.
-template <bool FACE>
+template <bool FACE, class LD = LdRO>
 __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double* __restrict__ y,
                                                int N, int n, int i, int j, int k, bool state,
                                                bool energy, int nw) {
   double g0[3], g1[3], g2[3];
   if (FACE) {
-    split_gcol(a, y, N, n, 0, i, a.nx, 1, g0);
-    split_gcol(a, y, N, n, 1, j, a.ny, a.nx, g1);
-    split_gcol(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
+    split_gcol<LD>(a, y, N, n, 0, i, a.nx, 1, g0);
+    split_gcol<LD>(a, y, N, n, 1, j, a.ny, a.nx, g1);
+    split_gcol<LD>(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
   } else {
     const int sy = a.nx, sz = a.nx * a.ny;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double* v = y + c * N;
-      g0[c] = __ldg(&v[n + 1]) - __ldg(&v[n - 1]);
-      g1[c] = __ldg(&v[n + sy]) - __ldg(&v[n - sy]);
-      g2[c] = __ldg(&v[n + sz]) - __ldg(&v[n - sz]);
+      g0[c] = LD::ld(&v[n + 1]) - LD::ld(&v[n - 1]);
+      g1[c] = LD::ld(&v[n + sy]) - LD::ld(&v[n - sy]);
+      g2[c] = LD::ld(&v[n + sz]) - LD::ld(&v[n - sz]);
     }
     g0[0] += a.h2[0];
     g1[1] += a.h2[1];
@@ -188,15 +207,11 @@ __device__ __forceinline__ double dot3_sub(const double a[3], const double b[3],
 // under predicates for every node, and predicated-off FP64 instructions
 // still take FP64-pipe slots; in the diagnostic launch also the energy
 // partials (eq. "magnetic energy").
-template <int S>
-__global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
-  pdl_wait();
-  const DevState* st = a.st;
-  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
-  __shared__ double red[8];
+template <int S, class LD>
+__device__ __forceinline__ void pass_B(const SplitArgs& a, int cur, double* red) {
   const int N = a.nx * a.ny * a.nz;
   const int NI = (a.nx - 2) * (a.ny - 2) * (a.nz - 2);
-  const double* y = S == 0 ? a.d[st->cur] : a.ys[S & 1];
+  const double* y = S == 0 ? a.d[cur] : a.ys[S & 1];
   const bool energy = S == 0 && a.diag;
   double eacc = 0.0;
   int tb, te;
@@ -205,7 +220,7 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
     const int n = interior_node(a, t, i, j, k);
-    eacc += split_B_node<false>(a, y, N, n, i, j, k, S == 0, energy, n);
+    eacc += split_B_node<false, LD>(a, y, N, n, i, j, k, S == 0, energy, n);
   }
   cta_range(N - NI, tb, te);
   for (int b = tb + threadIdx.x; b < te; b += blockDim.x) {
@@ -216,9 +231,9 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
       // Conditions"); it is not part of the period's energy
       const int kk = k == 0 ? a.nz - 2 : 1;
       const int np = (kk * a.ny + j) * a.nx + i;
-      split_B_node<true>(a, y, N, np, i, j, kk, S == 0, false, n);
+      split_B_node<true, LD>(a, y, N, np, i, j, kk, S == 0, false, n);
     } else {
-      eacc += split_B_node<true>(a, y, N, n, i, j, k, S == 0, energy, n);
+      eacc += split_B_node<true, LD>(a, y, N, n, i, j, k, S == 0, energy, n);
     }
   }
   pdl_trigger();
@@ -226,6 +241,15 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
     const double v = block_reduce<false>(eacc, red);
     if (threadIdx.x == 0) put_partial(a, PART_E, v);
   }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
+  pdl_wait();
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  __shared__ double red[8];
+  pass_B<S, LdRO>(a, st->cur, red);
 }
 
 // The next-nearest-neighbour current (section "Next Nearest Neighbor
@@ -240,12 +264,13 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
 // adjugate, J = (c_0 a_1 x a_2 + c_1 a_2 x a_0 + c_2 a_0 x a_1) / det M.
 // Positions are taken relative to the node: y (displacement) differences
 // plus the label offsets.
+template <class LD>
 __device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __restrict__ y,
                                             int N, int n, double J[3], double B[3]) {
   const int st[3] = {1, a.nx, a.nx * a.ny};
   double yc[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) yc[c] = __ldg(&y[c * N + n]);
+  for (int c = 0; c < 3; ++c) yc[c] = LD::ld(&y[c * N + n]);
   double M[3][3], cr[3];
 #pragma unroll 1
   for (int r = 0; r < 3; ++r) {
@@ -259,8 +284,8 @@ __device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __
       const int nn = n + op[m] * st[p] + oq[m] * st[q];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        xv[m][c] = __ldg(&y[c * N + nn]) - yc[c];
-        Bv[m][c] = __ldg(&a.Bb[c * N + nn]);
+        xv[m][c] = LD::ld(&y[c * N + nn]) - yc[c];
+        Bv[m][c] = LD::ld(&a.Bb[c * N + nn]);
       }
       xv[m][p] += 0.5 * op[m] * a.h2[p];
       xv[m][q] += 0.5 * oq[m] * a.h2[q];
@@ -318,7 +343,7 @@ __device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __
   for (int c = 0; c < 3; ++c)
     J[c] = (cr[0] * adj[0][c] + cr[1] * adj[1][c] + cr[2] * adj[2][c]) / detM;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) B[c] = __ldg(&a.Bb[c * N + n]);
+  for (int c = 0; c < 3; ++c) B[c] = LD::ld(&a.Bb[c * N + n]);
 }
 
 // Pass C (stage s): current and velocity at interior nodes; k_s and the
@@ -326,21 +351,17 @@ __device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __
 // nearest-neighbour current, held to 64 registers (four CTAs, 32 warps, per
 // SM); CURL 2: the next-nearest-neighbour current (a comparison option,
 // two CTAs per SM).
-template <int S, int CURL>
-__global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitArgs a) {
+template <int S, int CURL, class LD>
+__device__ __forceinline__ void pass_C(const SplitArgs& a, int cur, double* red) {
   constexpr bool FINAL = S == 5;
-  pdl_wait();
   const DevState* st = a.st;
-  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
-  __shared__ double red[8];
   const int N = a.nx * a.ny * a.nz;
-  const int cur = st->cur;
   const double* d = a.d[cur];
   double* dout = const_cast<double*>(a.d[cur ^ 1]);
   double* ynext = a.ys[(S + 1) & 1];
   double an[5];  // dt a_{S+1, j}: next stage input (non-final stages)
 #pragma unroll
-  for (int j = 0; j < 5; ++j) an[j] = (!FINAL && j <= S) ? st->dta[S + 1][j] : 0.0;
+  for (int j = 0; j < 5; ++j) an[j] = (!FINAL && j <= S) ? LD::ld(&st->dta[S + 1][j]) : 0.0;
   Acc<double> acc;
   const int sy = a.nx, sz = a.nx * a.ny;
   const int NI = (a.nx - 2) * (a.ny - 2) * (a.nz - 2);
@@ -351,12 +372,12 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
     const int n = interior_node(a, t, i, j, k);
     double J[3], B[3], u[3];
     if constexpr (CURL == 2) {
-      nnn_current(a, S == 0 ? d : a.ys[S & 1], N, n, J, B);
+      nnn_current<LD>(a, S == 0 ? d : a.ys[S & 1], N, n, J, B);
     } else {
       double g0[3], g1[3], g2[3], P0[3], P1[3], P2[3];
       const double2* q = reinterpret_cast<const double2*>(a.Gb + (size_t)n * 10);
-      const double2 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3),
-                    q4 = __ldg(q + 4);
+      const double2 q0 = LD::ld2(q), q1 = LD::ld2(q + 1), q2 = LD::ld2(q + 2),
+                    q3 = LD::ld2(q + 3), q4 = LD::ld2(q + 4);
       g0[0] = q0.x; g0[1] = q0.y; g0[2] = q1.x;
       g1[0] = q1.y; g1[1] = q2.x; g1[2] = q2.y;
       g2[0] = q3.x; g2[1] = q3.y; g2[2] = q4.x;
@@ -364,10 +385,10 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double* b = a.Bb + c * N;
-        P0[c] = __ldg(&b[n + 1]) - __ldg(&b[n - 1]);
-        P1[c] = __ldg(&b[n + sy]) - __ldg(&b[n - sy]);
-        P2[c] = __ldg(&b[n + sz]) - __ldg(&b[n - sz]);
-        B[c] = __ldg(&b[n]);
+        P0[c] = LD::ld(&b[n + 1]) - LD::ld(&b[n - 1]);
+        P1[c] = LD::ld(&b[n + sy]) - LD::ld(&b[n - sy]);
+        P2[c] = LD::ld(&b[n + sz]) - LD::ld(&b[n - sz]);
+        B[c] = LD::ld(&b[n]);
       }
       const double c0 = dot3_sub(P1, g2, P2, g1);
       const double c1 = dot3_sub(P2, g0, P0, g2);
@@ -384,9 +405,9 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
       for (int c = 0; c < 3; ++c) {
         a.k[S][c * N + n] = u[c];
         // next stage input y_{S+1} = d + sum_{j<=S} dt a_{S+1,j} k_j
-        double v = __ldg(&d[c * N + n]);
+        double v = LD::ld(&d[c * N + n]);
 #pragma unroll
-        for (int jj = 0; jj < S; ++jj) v = fma(an[jj], __ldg(&a.k[jj][c * N + n]), v);
+        for (int jj = 0; jj < S; ++jj) v = fma(an[jj], LD::ld(&a.k[jj][c * N + n]), v);
         v = fma(an[S], u[c], v);
         ynext[c * N + n] = v;
         // periodic in z: the ghost of an end plane holds the same
@@ -395,13 +416,15 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
           ynext[c * N + n + (k == 1 ? 1 : -1) * (a.nz - 2) * sz] = v;
       }
     } else {
-      const double b0 = st->dtb[0], b2 = st->dtb[2], b3 = st->dtb[3], b5 = st->dtb[5];
-      const double e0 = st->dte[0], e2 = st->dte[2], e3 = st->dte[3], e4 = st->dte[4],
-                   e5 = st->dte[5];
+      const double b0 = LD::ld(&st->dtb[0]), b2 = LD::ld(&st->dtb[2]),
+                   b3 = LD::ld(&st->dtb[3]), b5 = LD::ld(&st->dtb[5]);
+      const double e0 = LD::ld(&st->dte[0]), e2 = LD::ld(&st->dte[2]),
+                   e3 = LD::ld(&st->dte[3]), e4 = LD::ld(&st->dte[4]),
+                   e5 = LD::ld(&st->dte[5]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double k1 = __ldg(&a.k[0][c * N + n]), k3 = __ldg(&a.k[2][c * N + n]),
-                     k4 = __ldg(&a.k[3][c * N + n]), k5 = __ldg(&a.k[4][c * N + n]);
+        const double k1 = LD::ld(&a.k[0][c * N + n]), k3 = LD::ld(&a.k[2][c * N + n]),
+                     k4 = LD::ld(&a.k[3][c * N + n]), k5 = LD::ld(&a.k[4][c * N + n]);
         double up = b0 * k1;
         up = fma(b2, k3, up);
         up = fma(b3, k4, up);
@@ -411,7 +434,7 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
         er = fma(e3, k4, er);
         er = fma(e4, k5, er);
         er = fma(e5, u[c], er);
-        const double dn = __ldg(&d[c * N + n]) + up;
+        const double dn = LD::ld(&d[c * N + n]) + up;
         dout[c * N + n] = dn;
         if (a.periodic && (k == 1 || k == a.nz - 2))
           dout[c * N + n + (k == 1 ? 1 : -1) * (a.nz - 2) * sz] = dn;
@@ -431,6 +454,202 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
     v = block_reduce<true>(acc.xis2(), red);
     if (threadIdx.x == 0) put_partial(a, PART_XIS2, v);
   }
+}
+
+template <int S, int CURL>
+__global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitArgs a) {
+  pdl_wait();
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  __shared__ double red[8];
+  pass_C<S, CURL, LdRO>(a, st->cur, red);
+}
+
+// ---- persistent attempts ------------------------------------------------
+//
+// One cooperative launch runs whole attempts: the twelve passes and the
+// step control, with no kernel boundary between them.  Each CTA keeps the
+// node ranges it has in the per-pass kernels (the grid is the CTAs the SMs
+// hold, all resident), and instead of a grid-wide boundary after each pass
+// it waits only for the node planes its next pass reads:
+//   pass B of stage s at plane p reads the stage input at planes p-2..p+2,
+//     written by pass C of stage s-1 (the one-sided boundary stencil reaches
+//     two planes; the same wait orders pass C's earlier reads of the B, G
+//     and stage-input buffers that pass B now overwrites);
+//   pass C of stage s at plane p reads B at planes p-1..p+1 from pass B.
+// A CTA publishes a finished pass by adding one to the completion counter
+// of every plane its work touched (after a fence that makes its writes
+// visible at device scope); a wait reads the counters through L2 until they
+// reach (CTAs touching the plane) x (passes done).  The last CTA to finish
+// an attempt runs the step control and releases the others; the next
+// attempt's first pass reads the state the control selected.  All data
+// another CTA may have written is loaded through L2 (LdL2).  Every wait is
+// bounded: after 2 s it raises FLAG_TIMEOUT and status TIMEOUT and the CTA
+// leaves; the others see the flag in their own waits and leave too.
+// Results are bit-identical to the per-pass kernels: each node's
+// arithmetic is the same.
+
+constexpr unsigned long long PERSIST_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0: spin until *p >= want (bounded); false on timeout or abort.
+__device__ __forceinline__ bool persist_wait(const int* p, int want, DevState* st,
+                                             unsigned long long t0) {
+  for (;;) {
+    if (ld_acquire(p) >= want) return true;
+    if (ld_acquire(&st->flags) & FLAG_TIMEOUT) return false;
+    if (globaltimer_ns() - t0 > PERSIST_WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void persist_abort(DevState* st) {
+  atomicOr(&st->flags, FLAG_TIMEOUT);
+  atomicExch(&st->status, ST_TIMEOUT);
+}
+
+// Thread 0: wait for the counters of planes [lo - r, hi + r] (clipped to
+// [kmin, kmax]) of every interval to reach touch x phases.
+__device__ __forceinline__ bool persist_wait_planes(const int* iv, int nint, int r, int kmin,
+                                                    int kmax, const int* cnt, const int* touch,
+                                                    int phases, DevState* st) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (int q = 0; q < nint; ++q) {
+    const int lo = iv[2 * q], hi = iv[2 * q + 1];
+    if (lo > hi) continue;
+    for (int p = max(lo - r, kmin); p <= min(hi + r, kmax); ++p)
+      if (!persist_wait(&cnt[p], touch[p] * phases, st, t0)) return false;
+  }
+  return true;
+}
+
+// Thread 0: one completion for every plane of every interval.
+__device__ __forceinline__ void persist_publish(const int* iv, int nint, int* cnt) {
+  __threadfence();
+  for (int q = 0; q < nint; ++q)
+    for (int p = iv[2 * q]; p <= iv[2 * q + 1]; ++p) atomicAdd(&cnt[p], 1);
+}
+
+template <int CURL>
+__global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4)
+    k_attempts_persist(const SplitArgs a, const PersistArgs pa) {
+  __shared__ double red[8];
+  __shared__ double sh[96];
+  __shared__ int ok, last;
+  DevState* st = a.st;
+  const int G = gridDim.x;
+  const int* ivB = pa.ivB + blockIdx.x * 2 * PERSIST_BI;
+  const int* ivC = pa.ivC + blockIdx.x * 2;
+  for (int att = 0; att < pa.n_attempts; ++att) {
+    if (LdL2::ldi(&st->status) != ST_OK ||
+        __ldcg(&st->n_accept) >= __ldcg(&st->target))
+      return;
+    const int cur = LdL2::ldi(&st->cur);
+#define GLEMUR_PERSIST_STAGE(SS)                                                          \
+    if (SS > 0) {                                                                         \
+      if (threadIdx.x == 0)                                                               \
+        ok = persist_wait_planes(ivB, PERSIST_BI, 2, 1, a.nz - 2, pa.cntC, pa.touchC,     \
+                                 att * 6 + SS, st);                                       \
+      __syncthreads();                                                                    \
+      if (!ok) {                                                                          \
+        if (threadIdx.x == 0) persist_abort(st);                                          \
+        return;                                                                           \
+      }                                                                                   \
+    }                                                                                     \
+    pass_B<SS, LdL2>(a, cur, red);                                                        \
+    __syncthreads();                                                                      \
+    if (threadIdx.x == 0 && !(SS == 2 && (int)blockIdx.x == pa.test_withhold))            \
+      persist_publish(ivB, PERSIST_BI, pa.cntB);                                          \
+    if (threadIdx.x == 0)                                                                 \
+      ok = persist_wait_planes(ivC, 1, 1, 0, a.nz - 1, pa.cntB, pa.touchB,                \
+                               att * 6 + SS + 1, st);                                     \
+    __syncthreads();                                                                      \
+    if (!ok) {                                                                            \
+      if (threadIdx.x == 0) persist_abort(st);                                            \
+      return;                                                                             \
+    }                                                                                     \
+    pass_C<SS, CURL, LdL2>(a, cur, red);                                                  \
+    __syncthreads();                                                                      \
+    if (threadIdx.x == 0) persist_publish(ivC, 1, pa.cntC);
+    GLEMUR_PERSIST_STAGE(0)
+    GLEMUR_PERSIST_STAGE(1)
+    GLEMUR_PERSIST_STAGE(2)
+    GLEMUR_PERSIST_STAGE(3)
+    GLEMUR_PERSIST_STAGE(4)
+    GLEMUR_PERSIST_STAGE(5)
+#undef GLEMUR_PERSIST_STAGE
+    // end of the attempt: the last CTA to arrive runs the step control
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(&pa.bar[0], 1u);
+      last = old == (unsigned)(G * (att + 1) - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      control_block<LdCoherent>(st, a.part, a.nblocks, a.diag, pa.dtlog, sh);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&pa.bar[1], (unsigned)(att + 1));
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        ok = 1;
+        while (ld_acquire(&pa.bar[1]) < (unsigned)(att + 1)) {
+          if ((ld_acquire(&st->flags) & FLAG_TIMEOUT) ||
+              globaltimer_ns() - t0 > PERSIST_WAIT_NS) {
+            ok = 0;
+            break;
+          }
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (!ok) {
+        if (threadIdx.x == 0) persist_abort(st);
+        return;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// CTAs of 256 threads per SM the persistent kernel can hold, and its launch
+// (cooperative: every CTA resident, or the launch fails).
+int persist_ctas_per_sm(int curl) {
+  int n = 0;
+  if (curl == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_attempts_persist<2>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_attempts_persist<0>, 256, 0);
+  return n;
+}
+
+cudaError_t launch_f64_persist(const SplitArgs& a, const PersistArgs& pa, int grid, int curl,
+                               cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (curl == 2) return cudaLaunchKernelEx(&cfg, k_attempts_persist<2>, a, pa);
+  return cudaLaunchKernelEx(&cfg, k_attempts_persist<0>, a, pa);
 }
 
 // CTAs of 256 threads per SM that pass B and pass C of each stage can hold

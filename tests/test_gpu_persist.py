@@ -1,0 +1,105 @@
+"""Whole attempts in one persistent cooperative launch (FP64 two-pass
+stages, the default for line-tied FP64 contexts) against one launch per
+pass (GLEMUR_PERSIST=0): the same per-node arithmetic, so positions, step
+sizes, error norms and diagnostics agree bit for bit -- over controlled runs
+with rejections, for the nearest- and next-nearest-neighbour currents, on
+grids from one interior node to the 64^3 benchmark workload.  And the
+bounded waits: a CTA that never reports a finished pass makes its
+neighbours give up after 2 s with GLEMUR_ERR_TIMEOUT, without a fault; the
+device stays usable."""
+import time
+
+import numpy as np
+import pytest
+
+import glemur_inputs as gi
+import oracle as ora
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1405_0942_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def run(G, dims, curl, persist, monkeypatch, attempts=9):
+    monkeypatch.setenv("GLEMUR_PERSIST", "1" if persist else "0")
+    g = gi.Grid(*dims)
+    X = gi.nodes(g)
+    x0 = gi.predistort(X, 2)
+    B0 = gi.braid_field(X, gi.braid_regions(6, None, True))
+    r = G.Relaxation(g.nx, g.ny, g.nz, curl=curl, dt0=2e-2)
+    r.set_x(torch.from_numpy(x0).cuda())
+    r.set_B0(torch.from_numpy(B0).cuda())
+    assert (r.kernels_per_attempt() == 1) == persist
+    r.attempts(attempts)
+    st = r.stats()
+    x = r.get_x().cpu().numpy()
+    st2 = r.step(3)
+    x2 = r.get_x().cpu().numpy()
+    return st, x, st2, x2, r.energy(), r.forcefree_err()
+
+
+@pytest.mark.parametrize("curl", [0, 2], ids=["mimetic", "nnn"])
+@pytest.mark.parametrize("dims", [(3, 3, 3), (5, 4, 3), (20, 18, 16), (37, 19, 23),
+                                  (64, 64, 64)], ids=lambda d: "x".join(map(str, d)))
+def test_persistent_attempts_agree_bit_for_bit(G, dims, curl, monkeypatch):
+    a = run(G, dims, curl, True, monkeypatch)
+    b = run(G, dims, curl, False, monkeypatch)
+    assert a[0] == b[0] and a[2] == b[2]
+    assert a[0]["rejected"] > 0 or dims == (3, 3, 3)    # the control law is exercised
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
+    assert a[4] == b[4] and a[5] == b[5]
+
+
+def test_persistent_step_matches_oracle(G):
+    """The controlled steps of the persistent launch against the oracle's
+    (accept/reject sequence, step size, positions)."""
+    g = gi.Grid(14, 14, 14)
+    X = gi.nodes(g)
+    x0 = gi.predistort(X, 2)
+    B0 = gi.braid_field(X, gi.braid_regions(6, None, True))
+    opts = ora.ControlOpts(lambda0=1e-8)
+    x_ref, dt_ref, log, st_ref, rc = ora.relax(g, x0, B0, 20, 5e-2, opts=opts)
+    r = G.Relaxation(g.nx, g.ny, g.nz, lambda0=1e-8, dt0=5e-2)
+    assert r.kernels_per_attempt() == 1
+    r.set_x(torch.from_numpy(x0).cuda())
+    r.set_B0(torch.from_numpy(B0).cuda())
+    st = r.step(20)
+    assert st["accepted"] == 20 and st["rejected"] == st_ref["rejected"] > 0
+    assert abs(st["dt"] - dt_ref) < 1e-9 * dt_ref
+    x = r.get_x().cpu().numpy()
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() < 1e-11
+
+
+def test_persistent_wait_timeout_is_reported(G, monkeypatch):
+    g = gi.Grid(40, 36, 30)
+    X = gi.nodes(g)
+    x0 = gi.predistort(X, 2)
+    B0 = gi.braid_field(X, gi.braid_regions(6, None, True))
+    monkeypatch.setenv("GLEMUR_TEST_PERSIST_TIMEOUT", "1")
+    r = G.Relaxation(g.nx, g.ny, g.nz)
+    assert r.kernels_per_attempt() == 1
+    r.set_x(torch.from_numpy(x0).cuda())
+    r.set_B0(torch.from_numpy(B0).cuda())
+    t0 = time.time()
+    with pytest.raises(G.GlemurError) as err:
+        r.step(1)
+    assert err.value.code == -8 and time.time() - t0 < 60
+    st = r.stats()
+    assert st["status"] == -8 and st["accepted"] == 0
+    del r
+    monkeypatch.delenv("GLEMUR_TEST_PERSIST_TIMEOUT")
+    r2 = G.Relaxation(g.nx, g.ny, g.nz)
+    r2.set_x(torch.from_numpy(x0).cuda())
+    r2.set_B0(torch.from_numpy(B0).cuda())
+    u_ref, _ = ora.velocity(g, x0, B0)
+    assert np.abs(r2.velocity().cpu().numpy() - u_ref).max() < 1e-11 * np.abs(u_ref).max()
+    assert r2.step(2)["status"] == 0
