@@ -936,9 +936,10 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
       c->nblocks = c->split_grid_c[s] > c->nblocks ? c->split_grid_c[s] : c->nblocks;
     }
   }
-  // whole attempts in one persistent launch (FP64 two-pass stages, line-tied)
+  // whole attempts in one persistent launch (FP64 two-pass stages of the
+  // loop currents, line-tied)
   c->persist = 0;
-  if (c->split && !o.periodic_z) {
+  if (c->split && o.curl != GLEMUR_CURL_DIRECT && !o.periodic_z) {
     const char* pe = getenv("GLEMUR_PERSIST");
     if (!(pe && pe[0] == '0')) {
       const int per = persist_ctas_per_sm(o.curl == GLEMUR_CURL_NNN ? 2 : 0);

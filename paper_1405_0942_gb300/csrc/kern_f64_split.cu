@@ -502,7 +502,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// Thread 0: spin until *p >= want (bounded); false on timeout or abort.
+// Spin until *p >= want (bounded); false on timeout or abort.
 __device__ __forceinline__ bool persist_wait(const int* p, int want, DevState* st,
                                              unsigned long long t0) {
   for (;;) {
@@ -512,31 +512,54 @@ __device__ __forceinline__ bool persist_wait(const int* p, int want, DevState* s
   }
 }
 
+// The t-th plane of the intervals [lo - r, hi + r] (clipped to [kmin,
+// kmax]) taken in turn, or -1 past their end.
+__device__ __forceinline__ int persist_plane_at(const int* iv, int nint, int r, int kmin,
+                                                int kmax, int t) {
+  for (int q = 0; q < nint; ++q) {
+    const int lo = iv[2 * q], hi = iv[2 * q + 1];
+    if (lo > hi) continue;
+    const int a = max(lo - r, kmin), b = min(hi + r, kmax);
+    if (a > b) continue;
+    if (t <= b - a) return a + t;
+    t -= b - a + 1;
+  }
+  return -1;
+}
+
 __device__ __forceinline__ void persist_abort(DevState* st) {
   atomicOr(&st->flags, FLAG_TIMEOUT);
   atomicExch(&st->status, ST_TIMEOUT);
 }
 
-// Thread 0: wait for the counters of planes [lo - r, hi + r] (clipped to
-// [kmin, kmax]) of every interval to reach touch x phases.
+// The whole CTA: wait for the counters of planes [lo - r, hi + r] (clipped
+// to [kmin, kmax]) of every interval to reach touch x phases, one thread
+// per plane (a second round of planes per thread where there are more
+// planes than threads); true for every thread when all are reached.
 __device__ __forceinline__ bool persist_wait_planes(const int* iv, int nint, int r, int kmin,
                                                     int kmax, const int* cnt, const int* touch,
                                                     int phases, DevState* st) {
   const unsigned long long t0 = globaltimer_ns();
-  for (int q = 0; q < nint; ++q) {
-    const int lo = iv[2 * q], hi = iv[2 * q + 1];
-    if (lo > hi) continue;
-    for (int p = max(lo - r, kmin); p <= min(hi + r, kmax); ++p)
-      if (!persist_wait(&cnt[p], touch[p] * phases, st, t0)) return false;
+  bool ok = true;
+  for (int t = threadIdx.x;; t += blockDim.x) {
+    const int p = persist_plane_at(iv, nint, r, kmin, kmax, t);
+    if (p < 0) break;
+    ok = ok && persist_wait(&cnt[p], touch[p] * phases, st, t0);
   }
-  return true;
+  return __syncthreads_and(ok);
 }
 
-// Thread 0: one completion for every plane of every interval.
+// The whole CTA, after its pass: one completion for every plane of every
+// interval, one thread per plane, each after a device-scope fence (the
+// barrier before it makes the CTA's writes part of what the fence orders).
 __device__ __forceinline__ void persist_publish(const int* iv, int nint, int* cnt) {
-  __threadfence();
-  for (int q = 0; q < nint; ++q)
-    for (int p = iv[2 * q]; p <= iv[2 * q + 1]; ++p) atomicAdd(&cnt[p], 1);
+  __syncthreads();
+  for (int t = threadIdx.x;; t += blockDim.x) {
+    const int p = persist_plane_at(iv, nint, 0, 0, 1 << 30, t);
+    if (p < 0) break;
+    __threadfence();
+    atomicAdd(&cnt[p], 1);
+  }
 }
 
 template <int CURL>
@@ -555,31 +578,21 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4)
       return;
     const int cur = LdL2::ldi(&st->cur);
 #define GLEMUR_PERSIST_STAGE(SS)                                                          \
-    if (SS > 0) {                                                                         \
-      if (threadIdx.x == 0)                                                               \
-        ok = persist_wait_planes(ivB, PERSIST_BI, 2, 1, a.nz - 2, pa.cntC, pa.touchC,     \
-                                 att * 6 + SS, st);                                       \
-      __syncthreads();                                                                    \
-      if (!ok) {                                                                          \
-        if (threadIdx.x == 0) persist_abort(st);                                          \
-        return;                                                                           \
-      }                                                                                   \
+    if (SS > 0 && !persist_wait_planes(ivB, PERSIST_BI, 2, 1, a.nz - 2, pa.cntC,          \
+                                       pa.touchC, att * 6 + SS, st)) {                    \
+      if (threadIdx.x == 0) persist_abort(st);                                            \
+      return;                                                                             \
     }                                                                                     \
     pass_B<SS, LdL2>(a, cur, red);                                                        \
-    __syncthreads();                                                                      \
-    if (threadIdx.x == 0 && !(SS == 2 && (int)blockIdx.x == pa.test_withhold))            \
+    if (!(SS == 2 && (int)blockIdx.x == pa.test_withhold))                                \
       persist_publish(ivB, PERSIST_BI, pa.cntB);                                          \
-    if (threadIdx.x == 0)                                                                 \
-      ok = persist_wait_planes(ivC, 1, 1, 0, a.nz - 1, pa.cntB, pa.touchB,                \
-                               att * 6 + SS + 1, st);                                     \
-    __syncthreads();                                                                      \
-    if (!ok) {                                                                            \
+    if (!persist_wait_planes(ivC, 1, 1, 0, a.nz - 1, pa.cntB, pa.touchB,                  \
+                             att * 6 + SS + 1, st)) {                                     \
       if (threadIdx.x == 0) persist_abort(st);                                            \
       return;                                                                             \
     }                                                                                     \
     pass_C<SS, CURL, LdL2>(a, cur, red);                                                  \
-    __syncthreads();                                                                      \
-    if (threadIdx.x == 0) persist_publish(ivC, 1, pa.cntC);
+    persist_publish(ivC, 1, pa.cntC);
     GLEMUR_PERSIST_STAGE(0)
     GLEMUR_PERSIST_STAGE(1)
     GLEMUR_PERSIST_STAGE(2)
