@@ -937,11 +937,12 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
     }
   }
   // whole attempts in one persistent launch (FP64 two-pass stages of the
-  // loop currents, line-tied)
+  // loop currents, line-tied), on request: measured slower than the
+  // per-pass kernels chained by programmatic dependent launch
   c->persist = 0;
   if (c->split && o.curl != GLEMUR_CURL_DIRECT && !o.periodic_z) {
     const char* pe = getenv("GLEMUR_PERSIST");
-    if (!(pe && pe[0] == '0')) {
+    if (pe && atoi(pe) == 1) {
       const int per = persist_ctas_per_sm(o.curl == GLEMUR_CURL_NNN ? 2 : 0);
       long long G = (long long)per * c->nsm;
       const long long need = (c->N + 255) / 256;

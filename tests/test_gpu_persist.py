@@ -1,6 +1,6 @@
 """Whole attempts in one persistent cooperative launch (FP64 two-pass
-stages, the default for line-tied FP64 contexts) against one launch per
-pass (GLEMUR_PERSIST=0): the same per-node arithmetic, so positions, step
+stages, GLEMUR_PERSIST=1) against one launch per pass (the default): the
+same per-node arithmetic, so positions, step
 sizes, error norms and diagnostics agree bit for bit -- over controlled runs
 with rejections, for the nearest- and next-nearest-neighbour currents, on
 grids from one interior node to the 64^3 benchmark workload.  And the
@@ -70,7 +70,7 @@ def test_persistent_attempts_agree_bit_for_bit(G, dims, curl, monkeypatch):
     assert a[4] == b[4] and a[5] == b[5]
 
 
-def test_persistent_step_matches_oracle(G):
+def test_persistent_step_matches_oracle(G, monkeypatch):
     """The controlled steps of the persistent launch against the oracle's
     (accept/reject sequence, step size, positions)."""
     g = gi.Grid(14, 14, 14)
@@ -79,6 +79,7 @@ def test_persistent_step_matches_oracle(G):
     B0 = gi.braid_field(X, gi.braid_regions(6, None, True))
     opts = ora.ControlOpts(lambda0=1e-8)
     x_ref, dt_ref, log, st_ref, rc = ora.relax(g, x0, B0, 20, 5e-2, opts=opts)
+    monkeypatch.setenv("GLEMUR_PERSIST", "1")
     r = G.Relaxation(g.nx, g.ny, g.nz, lambda0=1e-8, dt0=5e-2)
     assert r.kernels_per_attempt() == 1
     r.set_x(torch.from_numpy(x0).cuda())
@@ -96,6 +97,7 @@ def test_persistent_wait_timeout_is_reported(G, monkeypatch):
     x0 = gi.predistort(X, 2)
     B0 = gi.braid_field(X, gi.braid_regions(6, None, True))
     monkeypatch.setenv("GLEMUR_TEST_PERSIST_TIMEOUT", "1")
+    monkeypatch.setenv("GLEMUR_PERSIST", "1")
     r = G.Relaxation(g.nx, g.ny, g.nz)
     assert r.kernels_per_attempt() == 1
     r.set_x(torch.from_numpy(x0).cuda())
