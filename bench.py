@@ -517,8 +517,8 @@ def our_arm(args):
         "data": "synthetic (seeded braid field and pre-distorted grid)",
         "config": config_dict(args, w), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
         "clocks": clocks,
-        # per timed attempt: the target reset plus the attempt's kernels
-        "gpu_launches": (r.kernels_per_attempt() + 1) * len(whole),
+        # the attempts' kernels (the step target is set once, in warm-up)
+        "gpu_launches": r.kernels_per_attempt() * len(whole),
         "kernel_ms": {"stages": per_kernel[:6], "control": per_kernel[6]},
         "attempts": {"accepted": st["accepted"], "rejected": st["rejected"]},
         "compare": extra,

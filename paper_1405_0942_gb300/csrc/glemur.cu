@@ -77,6 +77,7 @@ __global__ void k_reset_state(DevState* st, double dt0, double lambda0, double d
   st->flags = 0;
   st->max_rejects = max_rejects;
   st->replay = 0;
+  st->ticket = 0;
   st->E = st->xi = st->xi_sin = 0.0;
   set_coeffs(st);
 }
@@ -217,6 +218,7 @@ struct glemur_ctx {
   int nblocks_direct, kz_direct;         // direct-current launches
   dim3 grid, grid_direct;
   int nsm;
+  int target_unbounded;                  // the device's step target is LLONG_MAX
 };
 
 namespace {
@@ -430,7 +432,18 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.part = c->part;
   a.nblocks = c->nblocks;
   a.tma_test = c->tma_test;
+  a.ctl = 0;
+  a.ctl_diag = 0;
+  a.dtlog = c->dtlog;
   return a;
+}
+
+// Whether the last stage's kernel ends each attempt with the step control
+// (FP64 two-pass stages of the loop currents, mixed-precision TMA mimetic
+// stages), so no control kernel is launched.
+bool control_in_last_stage(const glemur_ctx* c) {
+  if (c->split && c->o.curl != GLEMUR_CURL_DIRECT) return true;
+  return c->o.precision == GLEMUR_MIXED && c->tma && c->o.curl == GLEMUR_CURL_MIMETIC;
 }
 
 int nblocks_of(const glemur_ctx* c, int curl) {
@@ -438,7 +451,7 @@ int nblocks_of(const glemur_ctx* c, int curl) {
 }
 
 cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, void* k6,
-                         int curl) {
+                         int curl, int ctl) {
   SplitArgs a;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -457,6 +470,9 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.diag = diag;
   a.force = force;
   a.periodic = c->o.periodic_z;
+  a.ctl = ctl;
+  a.ctl_diag = c->o.diag_each_attempt ? 1 : 0;
+  a.dtlog = c->dtlog;
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
@@ -468,9 +484,9 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
 }
 
 cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force,
-                         void* k6 = nullptr) {
+                         void* k6 = nullptr, int ctl = 0) {
   if (c->split && curl != GLEMUR_CURL_DIRECT)
-    return launch_split(c, stage, diag, force, k6, curl);
+    return launch_split(c, stage, diag, force, k6, curl, ctl);
   if (curl == GLEMUR_CURL_NNN) return cudaErrorInvalidValue;  // FP64 two-pass only
   const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
   if (c->o.precision == GLEMUR_MIXED) {
@@ -481,7 +497,11 @@ cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int
       a.nblocks = c->nblocks_direct;
       return launch_f32_direct(a, stage, g, c->s);
     }
-    if (c->tma) return launch_f32_mimetic_tma(a, c->maps, stage, g, c->s);
+    if (c->tma) {
+      a.ctl = ctl;
+      a.ctl_diag = c->o.diag_each_attempt ? 1 : 0;
+      return launch_f32_mimetic_tma(a, c->maps, stage, g, c->s);
+    }
     return launch_f32_mimetic(a, stage, g, c->s);
   }
   StageArgs<double> a = make_args<double>(c, stage, diag, force);
@@ -515,6 +535,9 @@ cudaError_t launch_attempts_persist(const glemur_ctx* c, int n) {
   a.diag = c->o.diag_each_attempt ? 1 : 0;
   a.force = 0;
   a.periodic = 0;
+  a.ctl = 0;  // the persistent kernel runs the control itself
+  a.ctl_diag = 0;
+  a.dtlog = c->dtlog;
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
@@ -532,10 +555,13 @@ cudaError_t launch_attempts_persist(const glemur_ctx* c, int n) {
 
 cudaError_t launch_attempt(const glemur_ctx* c) {
   const int diag = c->o.diag_each_attempt ? 1 : 0;
+  const bool fold = control_in_last_stage(c);
   for (int s = 0; s < 6; ++s) {
-    cudaError_t e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
+    cudaError_t e =
+        launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0, nullptr, s == 5 && fold ? 1 : 0);
     if (e != cudaSuccess) return e;
   }
+  if (fold) return cudaSuccess;
   return launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
                     nblocks_of(c, c->o.curl), diag, c->dtlog);
 }
@@ -594,6 +620,7 @@ int seed_stage_inputs(glemur_ctx* c) {
 }
 
 int reset_state(glemur_ctx* c) {
+  c->target_unbounded = 0;
   k_reset_state<<<1, 1, 0, c->s>>>(c->st, c->o.dt0, c->o.lambda0, c->o.dt_min, c->o.grow_max,
                                    c->o.shrink_min, c->o.max_rejects, c->o.safety);
   return cuda_rc(cudaGetLastError());
@@ -707,6 +734,7 @@ namespace glemur {
 // Leaves dt as the pending step size.
 int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6) {
   if (c->o.curl != GLEMUR_CURL_MIMETIC) return GLEMUR_ERR_BADARG;
+  c->target_unbounded = 0;
   k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 0);
   cudaError_t e = cudaGetLastError();
   for (int s = 0; s < 6 && e == cudaSuccess; ++s)
@@ -723,6 +751,7 @@ int ctx_recompute_stages(glemur_ctx* c, double dt, void* k6) {
 int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const* yS,
                                double* const* BS, double* const* RS) {
   if (c->o.curl != GLEMUR_CURL_MIMETIC || !c->split) return GLEMUR_ERR_BADARG;
+  c->target_unbounded = 0;
   k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 0);
   cudaError_t e = cudaGetLastError();
   for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
@@ -745,6 +774,9 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
     a.diag = 0;
     a.force = 1;
     a.periodic = 0;  // the adjoint refuses periodic contexts (ctx_info)
+    a.ctl = 0;
+    a.ctl_diag = 0;
+    a.dtlog = c->dtlog;
     a.st = c->st;
     a.part = c->part;
     a.nblocks = c->nblocks;
@@ -1059,8 +1091,12 @@ int glemur_velocity(glemur_ctx* c, double* u, int mem) {
 
 int glemur_attempts(glemur_ctx* c, int n_attempts) {
   if (!c || n_attempts < 0) return GLEMUR_ERR_BADARG;
-  k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (!c->target_unbounded) {
+    k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
+    e = cudaGetLastError();
+    c->target_unbounded = e == cudaSuccess;
+  }
   if (e == cudaSuccess) e = launch_attempts(c, n_attempts);
   return cuda_rc(e);
 }
@@ -1075,6 +1111,7 @@ int glemur_step(glemur_ctx* c, int n_accept, glemur_stats* stats) {
     return hs.status;
   }
   const long long target = hs.n_accept + n_accept;
+  c->target_unbounded = 0;
   k_set_target<<<1, 1, 0, c->s>>>(c->st, target, 0);
   if ((rc = cuda_rc(cudaGetLastError()))) return rc;
   while (hs.n_accept < target) {
@@ -1096,6 +1133,7 @@ int glemur_step_fixed(glemur_ctx* c, double dt, glemur_stats* stats) {
     fill_stats(hs, c->o.curl, stats);
     return hs.status;
   }
+  c->target_unbounded = 0;
   k_set_dt<<<1, 1, 0, c->s>>>(c->st, dt, 1);
   if ((rc = cuda_rc(cudaGetLastError()))) return rc;
   if ((rc = cuda_rc(launch_attempts(c, 1)))) return rc;
@@ -1169,7 +1207,8 @@ int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
 int glemur_kernels_per_attempt(const glemur_ctx* c) {
   if (!c) return 0;
   if (c->persist) return 1;
-  return c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 13 : 7;
+  const int per_stage = c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 2 : 1;
+  return 6 * per_stage + (control_in_last_stage(c) ? 0 : 1);
 }
 
 int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
@@ -1184,13 +1223,16 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   }
   k_set_target<<<1, 1, 0, c->s>>>(c->st, LLONG_MAX, 0);
   e = cudaGetLastError();
+  c->target_unbounded = e == cudaSuccess;
   const int diag = c->o.diag_each_attempt ? 1 : 0;
+  const bool fold = control_in_last_stage(c);
   for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
     e = cudaEventRecord(ev[s], c->s);
-    if (e == cudaSuccess) e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
+    if (e == cudaSuccess)
+      e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0, nullptr, s == 5 && fold ? 1 : 0);
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && !fold) {
     e = launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
                    nblocks_of(c, c->o.curl), diag, c->dtlog);
   }

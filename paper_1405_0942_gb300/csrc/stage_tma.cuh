@@ -15,6 +15,7 @@
 // independent stencils to overlap.
 #pragma once
 
+#include "control.cuh"
 #include "stage_kernels.cuh"
 
 namespace glemur {
@@ -232,14 +233,12 @@ __device__ __forceinline__ void tma_load_B0(const StageArgs<float>& a, int q,
 // hook (a.tma_test) adds a fourth barrier that no copy completes to the
 // prologue wait (1) or to the first wait inside the loop (2); the real
 // copies do complete, so the clean-up waits see them land.
-template <int WARPS, int R, int S, int MINB>
-__global__ void __launch_bounds__(32 * WARPS, MINB)
-    k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
+template <int WARPS, int R, int S>
+__device__ __forceinline__ void stage_mimetic_tma_body(const StageArgs<float>& a,
+                                                       const TmaMaps& maps) {
   using Gm = TmaGeo<WARPS, R>;
   constexpr bool FINAL = S == 5;
-  pdl_wait();
   const DevState* st = a.st;
-  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   if (st->flags & FLAG_TIMEOUT) return;  // an earlier stage of this attempt gave up
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -395,6 +394,18 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   if (__syncthreads_or(acc.bad) && threadIdx.x == 0)
     atomicOr(&a.st->flags, S == 0 ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   write_partials<float, float>(a, FINAL, diag, acc, red);
+}
+
+// The kernel: the body above (which may leave early on a timed-out wait),
+// then, in the last stage of an attempt, the end of the attempt.
+template <int WARPS, int R, int S, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB)
+    k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
+  pdl_wait();
+  const DevState* st = a.st;
+  if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
+  stage_mimetic_tma_body<WARPS, R, S>(a, maps);
+  if (S == 5 && a.ctl) attempt_end(a.st, a.part, a.nblocks, a.ctl_diag, a.dtlog);
 }
 
 // Launch stage `stage` (0..5) of the TMA mimetic kernel on `grid`.
