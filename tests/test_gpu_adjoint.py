@@ -245,14 +245,15 @@ def test_adjoint_96_cubed_500_steps_xi_vs_fd(G):
     """The 96^3 braid, 500 error-controlled steps (schedule frozen),
     checkpoints every 50: gradient of the final force-free error xi (taken at
     its argmax node) with respect to the 12 parameters against central
-    differences at h = 1e-3 relative.  xi (a maximum of second differences
-    of x) carries ~1e-12 relative rounding noise at this size, so smaller
-    steps are noise-limited (at h = 1e-4 and 5e-5 the errors of one
-    component were +1.8e-6 and -1.6e-6, and extrapolating between steps
-    amplifies that noise); at h = 1e-3 truncation stays near 1e-7.  xi is a
-    maximum: its difference quotient is the derivative only while the
-    argmax node stays put, so the node is checked at theta and at
-    theta +- h."""
+    differences of fourth order, (8 (L(h) - L(-h)) - (L(2h) - L(-2h))) / 12h
+    at h = 1e-3 relative.  xi (a maximum of second differences of x)
+    carries ~1e-12 relative rounding noise at this size, so small steps are
+    noise-limited (at h = 1e-4 the error of an amplitude component was
+    1.8e-6), while second-order differences at h = 1e-3 keep 2.5e-6 of
+    truncation error for the widths; the fourth-order formula removes that
+    at the larger step.  xi is a maximum: its difference quotient is the
+    derivative only while the argmax node stays put, so the node is checked
+    at theta and at every perturbed theta."""
     w = gi.make_workload("adjoint")
     g = w.grid
     X = gi.nodes(g)
@@ -268,26 +269,23 @@ def test_adjoint_96_cubed_500_steps_xi_vs_fd(G):
     theta = np.array(w.theta)
     m = len(w.regions)
     for p in range(len(theta)):
-        d = []
-        for rel in (1e-3,):
-            hh = rel * abs(theta[p])
-            vals = []
-            for sgn in (1, -1):
-                th = theta.copy()
-                th[p] += sgn * hh
-                regs = [(rr[0], rr[1], rr[2], th[i], th[m + i], rr[5])
-                        for i, rr in enumerate(w.regions)]
-                B0p = gi.braid_field(X, regs)
-                r.set_B0(cuda(B0p))
-                r.set_x(x0)
-                for dt in dts:
-                    r.step_fixed(dt)
-                vals.append(r.forcefree_err()[0])
-                assert _argmax_xi(G, r, g, B0p) == node0, (p, sgn, rel)
-            d.append((vals[0] - vals[1]) / (2 * hh))
-        d_fd = d[0]
+        hh = 1e-3 * abs(theta[p])
+        vals = {}
+        for mult in (1, -1, 2, -2):
+            th = theta.copy()
+            th[p] += mult * hh
+            regs = [(rr[0], rr[1], rr[2], th[i], th[m + i], rr[5])
+                    for i, rr in enumerate(w.regions)]
+            B0p = gi.braid_field(X, regs)
+            r.set_B0(cuda(B0p))
+            r.set_x(x0)
+            for dt in dts:
+                r.step_fixed(dt)
+            vals[mult] = r.forcefree_err()[0]
+            assert _argmax_xi(G, r, g, B0p) == node0, (p, mult)
+        d_fd = (8.0 * (vals[1] - vals[-1]) - (vals[2] - vals[-2])) / (12.0 * hh)
         assert abs(grad[p] - d_fd) < 1e-6 * max(abs(grad[p]), 1e-7 * value), \
-            (p, grad[p], d_fd, d)
+            (p, grad[p], d_fd)
     r.set_B0(cuda(w.B0))
 
 
