@@ -301,10 +301,9 @@ int glemur_convexity(glemur_ctx* ctx, long long* n_concave, signed char* kappa);
 int glemur_get_stats(glemur_ctx* ctx, glemur_stats* stats);
 
 /* Number of CUDA kernels one attempt launches (for launch accounting): the
- * stage kernels (two per stage for the FP64 two-pass stages) and, unless
- * the last stage's kernel runs it, the step-control kernel; 1 with the
- * persistent launch (GLEMUR_PERSIST=1, one launch for any number of
- * attempts). */
+ * stage kernels (two per stage for the FP64 two-pass stages) and the
+ * step-control kernel; 1 with the persistent launch (GLEMUR_PERSIST=1, one
+ * launch for any number of attempts). */
 int glemur_kernels_per_attempt(const glemur_ctx* ctx);
 
 /* Enqueue one attempt as glemur_attempts(ctx, 1) does (a target-reset
@@ -313,9 +312,8 @@ int glemur_kernels_per_attempt(const glemur_ctx* ctx);
  * recorded on the context's stream before each Cash-Karp stage, before the
  * step control and after it; synchronise and write the 7 intervals in
  * milliseconds to ms[0..6]: stages 1..6 (each interval covers all kernels
- * of its stage: two for the FP64 two-pass stages), then the control (about
- * zero where the last stage's kernel runs it).  Returns 7, or a negative
- * error (BADARG if cap < 7). */
+ * of its stage: two for the FP64 two-pass stages), then the control.
+ * Returns 7, or a negative error (BADARG if cap < 7). */
 int glemur_profile_attempt(glemur_ctx* ctx, float* ms, int cap);
 
 /* ---- adjoint (reverse mode) of the relaxation, mimetic current ---------

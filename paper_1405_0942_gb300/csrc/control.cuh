@@ -209,27 +209,4 @@ __device__ void control_block(DevState* st, const double* part, int nb, int diag
   if (go_on) set_coeffs_parallel(st, dt_next);
 }
 
-// End of an attempt inside the last stage's kernel: every CTA, once its own
-// partials are written, takes a ticket after a device-scope fence; the CTA
-// that takes the last ticket has every other CTA's partials visible and
-// runs the step control (no CTA waits for another), then resets the ticket
-// for the next attempt.
-__device__ __forceinline__ void attempt_end(DevState* st, const double* part, int nb, int diag,
-                                            double* dtlog) {
-  __shared__ int is_last;
-  __shared__ double sh[96];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned nct = gridDim.x * gridDim.y * gridDim.z;
-    is_last = atomicAdd(&st->ticket, 1u) == nct - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  control_block<LdCoherent>(st, part, nb, diag, dtlog, sh);
-  __syncthreads();
-  if (threadIdx.x == 0) st->ticket = 0;
-}
-
 }  // namespace glemur

@@ -77,7 +77,6 @@ __global__ void k_reset_state(DevState* st, double dt0, double lambda0, double d
   st->flags = 0;
   st->max_rejects = max_rejects;
   st->replay = 0;
-  st->ticket = 0;
   st->E = st->xi = st->xi_sin = 0.0;
   set_coeffs(st);
 }
@@ -432,25 +431,15 @@ StageArgs<T> make_args(const glemur_ctx* c, int stage, int diag, int force) {
   a.part = c->part;
   a.nblocks = c->nblocks;
   a.tma_test = c->tma_test;
-  a.ctl = 0;
-  a.ctl_diag = 0;
-  a.dtlog = c->dtlog;
   return a;
 }
-
-// Whether the last stage's kernel ends each attempt with the step control
-// (the CTA that finishes last runs it) instead of a control kernel.  Off:
-// measured slower than the control kernel launched as a programmatic
-// dependent, which is resident when the last stage ends (FP64 braid 64^3
-// unchanged, mixed 64^3 5 % slower); the kernels keep the option (ctl).
-bool control_in_last_stage(const glemur_ctx*) { return false; }
 
 int nblocks_of(const glemur_ctx* c, int curl) {
   return curl == GLEMUR_CURL_DIRECT ? c->nblocks_direct : c->nblocks;
 }
 
 cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, void* k6,
-                         int curl, int ctl) {
+                         int curl) {
   SplitArgs a;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -469,9 +458,6 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
   a.diag = diag;
   a.force = force;
   a.periodic = c->o.periodic_z;
-  a.ctl = ctl;
-  a.ctl_diag = c->o.diag_each_attempt ? 1 : 0;
-  a.dtlog = c->dtlog;
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
@@ -483,9 +469,9 @@ cudaError_t launch_split(const glemur_ctx* c, int stage, int diag, int force, vo
 }
 
 cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int force,
-                         void* k6 = nullptr, int ctl = 0) {
+                         void* k6 = nullptr) {
   if (c->split && curl != GLEMUR_CURL_DIRECT)
-    return launch_split(c, stage, diag, force, k6, curl, ctl);
+    return launch_split(c, stage, diag, force, k6, curl);
   if (curl == GLEMUR_CURL_NNN) return cudaErrorInvalidValue;  // FP64 two-pass only
   const dim3 g = curl == GLEMUR_CURL_DIRECT ? c->grid_direct : c->grid;
   if (c->o.precision == GLEMUR_MIXED) {
@@ -496,11 +482,7 @@ cudaError_t launch_stage(const glemur_ctx* c, int curl, int stage, int diag, int
       a.nblocks = c->nblocks_direct;
       return launch_f32_direct(a, stage, g, c->s);
     }
-    if (c->tma) {
-      a.ctl = ctl;
-      a.ctl_diag = c->o.diag_each_attempt ? 1 : 0;
-      return launch_f32_mimetic_tma(a, c->maps, stage, g, c->s);
-    }
+    if (c->tma) return launch_f32_mimetic_tma(a, c->maps, stage, g, c->s);
     return launch_f32_mimetic(a, stage, g, c->s);
   }
   StageArgs<double> a = make_args<double>(c, stage, diag, force);
@@ -534,9 +516,6 @@ cudaError_t launch_attempts_persist(const glemur_ctx* c, int n) {
   a.diag = c->o.diag_each_attempt ? 1 : 0;
   a.force = 0;
   a.periodic = 0;
-  a.ctl = 0;  // the persistent kernel runs the control itself
-  a.ctl_diag = 0;
-  a.dtlog = c->dtlog;
   a.st = c->st;
   a.part = c->part;
   a.nblocks = c->nblocks;
@@ -554,13 +533,10 @@ cudaError_t launch_attempts_persist(const glemur_ctx* c, int n) {
 
 cudaError_t launch_attempt(const glemur_ctx* c) {
   const int diag = c->o.diag_each_attempt ? 1 : 0;
-  const bool fold = control_in_last_stage(c);
   for (int s = 0; s < 6; ++s) {
-    cudaError_t e =
-        launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0, nullptr, s == 5 && fold ? 1 : 0);
+    cudaError_t e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
     if (e != cudaSuccess) return e;
   }
-  if (fold) return cudaSuccess;
   return launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
                     nblocks_of(c, c->o.curl), diag, c->dtlog);
 }
@@ -773,9 +749,6 @@ int ctx_recompute_stages_saved(glemur_ctx* c, double dt, void* k6, double* const
     a.diag = 0;
     a.force = 1;
     a.periodic = 0;  // the adjoint refuses periodic contexts (ctx_info)
-    a.ctl = 0;
-    a.ctl_diag = 0;
-    a.dtlog = c->dtlog;
     a.st = c->st;
     a.part = c->part;
     a.nblocks = c->nblocks;
@@ -1206,8 +1179,7 @@ int glemur_get_stats(glemur_ctx* c, glemur_stats* stats) {
 int glemur_kernels_per_attempt(const glemur_ctx* c) {
   if (!c) return 0;
   if (c->persist) return 1;
-  const int per_stage = c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 2 : 1;
-  return 6 * per_stage + (control_in_last_stage(c) ? 0 : 1);
+  return c->split && c->o.curl != GLEMUR_CURL_DIRECT ? 13 : 7;
 }
 
 int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
@@ -1224,14 +1196,12 @@ int glemur_profile_attempt(glemur_ctx* c, float* ms, int cap) {
   e = cudaGetLastError();
   c->target_unbounded = e == cudaSuccess;
   const int diag = c->o.diag_each_attempt ? 1 : 0;
-  const bool fold = control_in_last_stage(c);
   for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
     e = cudaEventRecord(ev[s], c->s);
-    if (e == cudaSuccess)
-      e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0, nullptr, s == 5 && fold ? 1 : 0);
+    if (e == cudaSuccess) e = launch_stage(c, c->o.curl, s, s == 0 ? diag : 0, 0);
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->s);
-  if (e == cudaSuccess && !fold) {
+  if (e == cudaSuccess) {
     e = launch_pdl(k_control, dim3(1), dim3(256), 0, c->s, c->st, (const double*)c->part,
                    nblocks_of(c, c->o.curl), diag, c->dtlog);
   }

@@ -71,7 +71,6 @@ struct DevState {
   unsigned flags;     // FLAG_* raised by stage kernels in this attempt
   int max_rejects;
   int replay;         // 1: accept the next attempt whatever its error
-  unsigned ticket;    // CTAs of the last stage done with this attempt
   // dt-scaled Cash-Karp coefficients of the pending attempt
   double dta[6][6];
   double dtb[6];
@@ -104,10 +103,6 @@ struct StageArgs {
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;
-  // the last stage's CTAs end the attempt: the last one runs the step
-  // control (with the diagnostics of the attempt's first stage if ctl_diag)
-  int ctl, ctl_diag;
-  double* dtlog;       // accepted step-size ring (the control writes it)
   // test hook of the bounded tile waits: 0 (off); 1 or 2 make the TMA
   // stage kernels also wait, at the prologue (1) or at the first wait
   // inside the plane loop (2), on a barrier that no copy completes, so that
@@ -169,8 +164,6 @@ struct SplitArgs {
                        // written by pass B, read by pass C
   int diag, force;
   int periodic;        // periodic in z: planes 0, nz-1 are ghosts of nz-2, 1
-  int ctl, ctl_diag;   // as in StageArgs: pass C of the last stage ends the
-  double* dtlog;       // attempt with the step control
   DevState* st;
   double* part;        // [NPART][nblocks] per-CTA partials
   int nblocks;         // partial stride: the largest of the grids

@@ -480,7 +480,6 @@ __global__ void __launch_bounds__(256, CURL == 2 ? 2 : 4) k_split_C(const SplitA
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   __shared__ double red[8];
   pass_C<S, CURL, LdRO>(a, st->cur, red);
-  if (S == 5 && a.ctl) attempt_end(a.st, a.part, a.nblocks, a.ctl_diag, a.dtlog);
 }
 
 // ---- persistent attempts ------------------------------------------------

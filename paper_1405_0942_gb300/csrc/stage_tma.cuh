@@ -15,7 +15,6 @@
 // independent stencils to overlap.
 #pragma once
 
-#include "control.cuh"
 #include "stage_kernels.cuh"
 
 namespace glemur {
@@ -396,8 +395,7 @@ __device__ __forceinline__ void stage_mimetic_tma_body(const StageArgs<float>& a
   write_partials<float, float>(a, FINAL, diag, acc, red);
 }
 
-// The kernel: the body above (which may leave early on a timed-out wait),
-// then, in the last stage of an attempt, the end of the attempt.
+// The kernel: the body above (which may leave early on a timed-out wait).
 template <int WARPS, int R, int S, int MINB>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_stage_mimetic_tma(const StageArgs<float> a, const __grid_constant__ TmaMaps maps) {
@@ -405,7 +403,6 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
   stage_mimetic_tma_body<WARPS, R, S>(a, maps);
-  if (S == 5 && a.ctl) attempt_end(a.st, a.part, a.nblocks, a.ctl_diag, a.dtlog);
 }
 
 // Launch stage `stage` (0..5) of the TMA mimetic kernel on `grid`.
