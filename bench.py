@@ -56,6 +56,11 @@ MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # captured from (kernel_source_hash()); a workload without an entry, or one
 # whose kernels have changed since, reports null
 NCU_TRAFFIC = {
+    (64, "fp64", "mimetic"): (58536491, "795a5dc3b9f8"),
+    (64, "fp64", "direct"): (31328981, "795a5dc3b9f8"),
+    (64, "mixed", "mimetic"): (15707221, "795a5dc3b9f8"),
+    (64, "mixed", "direct"): (15825451, "795a5dc3b9f8"),
+    (128, "mixed", "mimetic"): (155372715, "795a5dc3b9f8"),
 }
 
 
