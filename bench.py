@@ -30,6 +30,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 import numpy as np
 
@@ -46,21 +47,21 @@ UNIT = "node-stage/s"
 ALGO_BYTES = {"fp64": 132.0, "mixed": 66.0}
 # FP64 flops per interior node-stage of the mimetic stage kernel (FMA = 2),
 # counted once per node (halo recomputation excluded)
-ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0}
+ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0, "nnn": 861.0}
 FP64_PEAK_FLOPS = 1.25e12      # nominal dense FP64 rate of GB300 (152 SMs)
 L2_FLUSH_BYTES = 512 << 20
 MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # DRAM bytes per stage from ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # of one attempt's six stages, averaged; FP64: both passes of a stage), keyed
-# by (n, precision, curl), with the hash of the kernel sources they were
+# by (workload, precision, curl), with the hash of the kernel sources they were
 # captured from (kernel_source_hash()); a workload without an entry, or one
 # whose kernels have changed since, reports null
 NCU_TRAFFIC = {
-    (64, "fp64", "mimetic"): (58536491, "795a5dc3b9f8"),
-    (64, "fp64", "direct"): (31328981, "795a5dc3b9f8"),
-    (64, "mixed", "mimetic"): (15707221, "795a5dc3b9f8"),
-    (64, "mixed", "direct"): (15825451, "795a5dc3b9f8"),
-    (128, "mixed", "mimetic"): (155372715, "795a5dc3b9f8"),
+    ("braid64", "fp64", "mimetic"): (58536491, "795a5dc3b9f8"),
+    ("braid64", "fp64", "direct"): (31328981, "795a5dc3b9f8"),
+    ("braid64", "mixed", "mimetic"): (15707221, "795a5dc3b9f8"),
+    ("braid64", "mixed", "direct"): (15825451, "795a5dc3b9f8"),
+    ("braid128", "mixed", "mimetic"): (155372715, "795a5dc3b9f8"),
 }
 
 
@@ -77,8 +78,8 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(n, precision, curl):
-    ent = NCU_TRAFFIC.get((n, precision, curl))
+def ncu_traffic(name, precision, curl):
+    ent = NCU_TRAFFIC.get((name, precision, curl))
     if ent is None or ent[1] != kernel_source_hash():
         return None
     return ent[0]
@@ -168,17 +169,43 @@ def reduce_over_ranks(seconds, units, world, device):
     return float(t.item()), int(round(u.item()))
 
 
+# z-periodic counterpart of the 64^3 braid: 64 x 64 nodes across, 62 inner
+# planes between the two ghost planes (the same 238,328 interior nodes)
+PERIODIC_WORKLOADS = {"periodic64": 64}
+
+
 def workload(name, n=None):
+    if name in PERIODIC_WORKLOADS:
+        m = n or PERIODIC_WORKLOADS[name]
+        g, x0, B0 = gi.periodic_case(m, m, m - 2, h_z=2.0 / (m - 1))
+        return types.SimpleNamespace(grid=g, x0=x0, B0=B0)
     base, nn, _ = gi.WORKLOADS[name]
     return gi.make_workload(base, n=n or nn)
 
 
+def curl_const(G, curl):
+    return {"mimetic": G.MIMETIC, "direct": G.DIRECT, "nnn": G.NNN}[curl]
+
+
+def new_relaxation(G, w, precision, curl):
+    g = w.grid
+    return G.Relaxation(g.nx, g.ny, g.nz, g.lo, g.hi,
+                        precision=G.MIXED if precision == "mixed" else G.FP64,
+                        curl=curl_const(G, curl), periodic_z=1 if g.periodic_z else 0)
+
+
 def config_dict(args, w):
     g = w.grid
+    if args.workload.startswith("braid"):
+        fields = "braid of twist regions on a seeded pre-distorted grid"
+    elif args.workload in PERIODIC_WORKLOADS:
+        fields = ("two z-periodic twist regions on e_z, periodically pre-distorted grid, "
+                  "periodic z boundaries (ghost planes one period from their partners)")
+    else:
+        fields = args.workload
     return {"workload": args.workload, "grid": [g.nx, g.ny, g.nz],
             "interior_nodes": g.n_interior, "precision": args.precision, "curl": args.curl,
-            "fields": "braid of twist regions on a seeded pre-distorted grid" if
-            args.workload.startswith("braid") else args.workload,
+            "fields": fields,
             "step": "one Cash-Karp attempt (6 stages + update/error + control)",
             "l2": "flushed between timed steps (512 MiB write)",
             "lambda0": 1e-7}
@@ -193,7 +220,7 @@ def run_oracle_sample(w, max_seconds, max_steps, curl):
     import oracle as ora
     g = w.grid
     x = w.x0.copy()
-    c = ora.MIMETIC if curl == "mimetic" else ora.DIRECT
+    c = {"mimetic": ora.MIMETIC, "direct": ora.DIRECT, "nnn": ora.NNN}[curl]
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps:
@@ -264,9 +291,7 @@ def time_mode(G, torch, w, precision, curl, steps, warmup, flush, min_s=MIN_TIME
     launch order: six stages and the step control) of `steps` more attempts
     with an event between stages; those events keep each stage from starting
     early, so the split adds up to a little more than the whole attempt."""
-    r = G.Relaxation(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.lo, w.grid.hi,
-                     precision=G.MIXED if precision == "mixed" else G.FP64,
-                     curl=G.DIRECT if curl == "direct" else G.MIMETIC)
+    r = new_relaxation(G, w, precision, curl)
     r.set_x(torch.from_numpy(w.x0).cuda())
     r.set_B0(torch.from_numpy(w.B0).cuda())
     for _ in range(warmup):
@@ -321,7 +346,7 @@ def fp64_context(torch):
                         dgemm_tflops=2.0 * n ** 3 / (best * 1e-3) / 1e12)
 
 
-def roofline_entry(whole, split, w, precision, curl, hbm_peak, peak_kind):
+def roofline_entry(whole, split, w, name, precision, curl, hbm_peak, peak_kind):
     """Roofline of the stage launches.  Duration basis: the whole timed
     attempt (six stage launches, the step control and the target reset), so
     the achieved rate is a lower bound for the stages themselves; the
@@ -330,7 +355,7 @@ def roofline_entry(whole, split, w, precision, curl, hbm_peak, peak_kind):
     I = w.grid.n_interior
     bytes_per_attempt = ALGO_BYTES[precision] * I * 6
     gbs = bytes_per_attempt / (att_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(w.grid.nx, precision, curl)
+    traffic = ncu_traffic(name, precision, curl)
     shares = (split[:, :6].mean(axis=0) / split.sum(axis=1).mean()).round(4).tolist()
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
            "frac": gbs / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -399,9 +424,7 @@ def adjoint_measure(G, torch, w, precision, steps, flush, hbm_peak, peak_kind):
 def e2e_measure(G, torch, w, precision, curl, steps):
     """Same step through the C ABI with host buffers: H2D of x and B0 from
     pinned memory, the attempt, D2H of the new positions, per step."""
-    r = G.Relaxation(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.lo, w.grid.hi,
-                     precision=G.MIXED if precision == "mixed" else G.FP64,
-                     curl=G.DIRECT if curl == "direct" else G.MIMETIC)
+    r = new_relaxation(G, w, precision, curl)
     xh = torch.from_numpy(w.x0).pin_memory()
     bh = torch.from_numpy(w.B0).pin_memory()
     out = torch.empty_like(xh).pin_memory()
@@ -457,7 +480,8 @@ def our_arm(args):
     total_s, units = reduce_over_ranks(whole.sum() * 1e-3, w.grid.n_interior * 6 * len(whole),
                                        ws, "cuda")
     value = units / total_s
-    roof = roofline_entry(whole, split, w, args.precision, args.curl, hbm_peak, peak_kind)
+    roof = roofline_entry(whole, split, w, args.workload, args.precision, args.curl, hbm_peak,
+                          peak_kind)
     per_kernel = split.mean(axis=0).tolist()
 
     extra = {}
@@ -471,7 +495,24 @@ def our_arm(args):
             extra[f"{prec}_{curl}"] = {
                 "value": v2, "unit": UNIT, "ms_per_step": ms2.mean(),
                 "speedup_vs_primary": v2 / value,
-                "roofline": roofline_entry(ms2, sp2, w, prec, curl, hbm_peak, peak_kind)}
+                "roofline": roofline_entry(ms2, sp2, w, args.workload, prec, curl, hbm_peak,
+                                           peak_kind)}
+        if args.workload == "braid64" and args.precision == "fp64":
+            # the FP64 two-pass stages with the next-nearest-neighbour
+            # current on the same workload, and with periodic z boundaries
+            # on its z-periodic counterpart
+            for name, curl in (("braid64", "nnn"), ("periodic64", "mimetic")):
+                wl = w if name == "braid64" else workload(name)
+                _, ms4, sp4, _ = time_mode(G, torch, wl, "fp64", curl, args.steps,
+                                           args.warmup, flush, args.min_seconds)
+                v4 = wl.grid.n_interior * 6 / (ms4.mean() * 1e-3)
+                key = "fp64_nnn" if curl == "nnn" else "fp64_mimetic_periodic64"
+                extra[key] = {
+                    "value": v4, "unit": UNIT, "ms_per_step": ms4.mean(),
+                    "speedup_vs_primary": v4 / value, "workload": name,
+                    "grid": [wl.grid.nx, wl.grid.ny, wl.grid.nz],
+                    "roofline": roofline_entry(ms4, sp4, wl, name, "fp64", curl, hbm_peak,
+                                               peak_kind)}
         if args.workload == "braid64":
             # the mixed-precision path where HBM, not L2, holds the fields:
             # the 128^3 braid of 10 twist regions (mixed-precision workload)
@@ -485,7 +526,7 @@ def our_arm(args):
                     "value": v3, "unit": UNIT, "ms_per_step": ms3.mean(),
                     "timed_attempts": len(ms3), "workload": name,
                     "grid": [wl.grid.nx, wl.grid.ny, wl.grid.nz],
-                    "roofline": roofline_entry(ms3, sp3, wl, "mixed", "mimetic", hbm_peak,
+                    "roofline": roofline_entry(ms3, sp3, wl, name, "mixed", "mimetic", hbm_peak,
                                                peak_kind)}
                 del r3, wl
                 torch.cuda.empty_cache()
@@ -553,9 +594,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="braid64", choices=sorted(gi.WORKLOADS))
+    ap.add_argument("--workload", default="braid64",
+                    choices=sorted(gi.WORKLOADS) + sorted(PERIODIC_WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--curl", default="mimetic", choices=["mimetic", "direct"])
+    ap.add_argument("--curl", default="mimetic", choices=["mimetic", "direct", "nnn"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the reverse step (glemur_vjp_step) and print its line")

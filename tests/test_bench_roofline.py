@@ -22,13 +22,13 @@ def test_mixed_roofline_is_bytes_over_whole_attempt():
     w = _W(128)
     whole = np.array([0.35, 0.35])                     # ms per attempt
     split = np.array([[0.06] * 6 + [0.01]] * 2)        # six stages + control
-    r = bench.roofline_entry(whole, split, w, "mixed", "mimetic", 6783.8, "measured")
+    r = bench.roofline_entry(whole, split, w, "braid128", "mixed", "mimetic", 6783.8, "measured")
     I = 126 ** 3
     gbs = 66.0 * I * 6 / (0.35e-3) / 1e9
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert np.isclose(r["achieved"], gbs) and np.isclose(r["frac"], gbs / 6783.8)
     assert r["algorithmic_bytes_per_launch"] == 66.0 * I
-    ent = bench.NCU_TRAFFIC.get((128, "mixed", "mimetic"))
+    ent = bench.NCU_TRAFFIC.get(("braid128", "mixed", "mimetic"))
     fresh = ent is not None and ent[1] == bench.kernel_source_hash()
     assert r["traffic"] == (ent[0] if fresh else None)
     assert np.isclose(sum(r["stage_shares"]), 0.36 / 0.37, atol=1e-3)
@@ -38,7 +38,7 @@ def test_fp64_roofline_is_flops_against_the_fp64_rate():
     w = _W(64)
     whole = np.array([0.4])
     split = np.array([[0.07] * 6 + [0.01]])
-    r = bench.roofline_entry(whole, split, w, "fp64", "mimetic", 6783.8, "measured")
+    r = bench.roofline_entry(whole, split, w, "braid64", "fp64", "mimetic", 6783.8, "measured")
     I = 62 ** 3
     tf = bench.ALGO_FLOPS_F64["mimetic"] * I * 6 / 0.4e-3 / 1e12
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
@@ -48,8 +48,8 @@ def test_fp64_roofline_is_flops_against_the_fp64_rate():
 
 
 def test_workload_without_a_capture_reports_null_traffic():
-    r = bench.roofline_entry(np.array([1.0]), np.array([[0.1] * 7]), _W(96), "mixed",
-                             "direct", 6783.8, "measured")
+    r = bench.roofline_entry(np.array([1.0]), np.array([[0.1] * 7]), _W(96), "adjoint96",
+                             "mixed", "direct", 6783.8, "measured")
     assert r["traffic"] is None
 
 
@@ -58,7 +58,15 @@ def test_traffic_goes_null_when_the_kernels_change(monkeypatch):
     captured on: an entry carrying another source hash reads as null."""
     h = bench.kernel_source_hash()
     assert len(h) == 12
-    monkeypatch.setitem(bench.NCU_TRAFFIC, (40, "mixed", "mimetic"), (1.5e6, h))
-    monkeypatch.setitem(bench.NCU_TRAFFIC, (41, "mixed", "mimetic"), (1.5e6, "0" * 12))
-    assert bench.ncu_traffic(40, "mixed", "mimetic") == 1.5e6
-    assert bench.ncu_traffic(41, "mixed", "mimetic") is None
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("w40", "mixed", "mimetic"), (1.5e6, h))
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("w41", "mixed", "mimetic"), (1.5e6, "0" * 12))
+    assert bench.ncu_traffic("w40", "mixed", "mimetic") == 1.5e6
+    assert bench.ncu_traffic("w41", "mixed", "mimetic") is None
+
+
+def test_nnn_roofline_uses_its_own_flop_count():
+    r = bench.roofline_entry(np.array([1.0]), np.array([[0.15] * 6 + [0.01]]), _W(64),
+                             "braid64", "fp64", "nnn", 6783.8, "measured")
+    I = 62 ** 3
+    assert np.isclose(r["achieved"], 861.0 * I * 6 / 1e-3 / 1e12)
+    assert r["algorithmic_flops_per_launch"] == 861.0 * I

@@ -184,7 +184,7 @@ def test_autograd_over_parameters(G, loss):
     for dt in dts:
         r.step_fixed(dt)
     ref_val = r.energy() if loss == 0 else r.forcefree_err()[0]
-    assert float(L) == pytest.approx(ref_val, rel=1e-14)
+    assert float(L.detach()) == pytest.approx(ref_val, rel=1e-14)
     (2.0 * L).backward()
     assert len(calls) == len(dts)
     B0, dB = field(theta.detach())

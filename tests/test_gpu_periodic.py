@@ -62,6 +62,24 @@ def test_velocity_and_step_periodic(G, case, curl):
     assert np.abs(x[:2, -1] - x[:2, 1]).max() < 1e-14
 
 
+@pytest.mark.parametrize("curl", [0, 2], ids=["mimetic", "nnn"])
+def test_periodic_benchmark_size(G, curl):
+    """The z-periodic 64^3 workload the benchmark times (64 x 64 nodes
+    across, 62 inner planes), one step, in the benchmark's launch
+    configuration (one wave of CTAs, threads taking several nodes)."""
+    g, x0, B0 = gi.periodic_case(64, 64, 62, h_z=2.0 / 63.0)
+    dt = 3e-4
+    x_ref, lam_ref, rc = ora.step_fixed(g, x0, B0, dt, curl)
+    assert rc == ora.OK
+    r = relaxation(G, g, x0, B0, curl=curl)
+    st = r.step_fixed(dt)
+    assert st["accepted"] == 1
+    x = r.get_x().cpu().numpy()
+    assert rel_inf(x, x_ref) < 1e-12
+    assert np.abs(x - x_ref).max() < 1e-9 * np.abs(x_ref - x0).max()
+    assert abs(st["lam"] - lam_ref) <= 1e-9 * lam_ref + 1e-15 * np.abs(x_ref - x0).max()
+
+
 def test_periodic_hundred_steps_replayed_and_control(G):
     g, x0, B0 = gi.periodic_case(14, 12, 20)
     x_ref, dt_ref, log, st_ref, rc = ora.relax(g, x0, B0, 100, 1e-3)
