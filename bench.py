@@ -47,7 +47,7 @@ UNIT = "node-stage/s"
 ALGO_BYTES = {"fp64": 132.0, "mixed": 66.0}
 # FP64 flops per interior node-stage of the mimetic stage kernel (FMA = 2),
 # counted once per node (halo recomputation excluded)
-ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0, "nnn": 861.0}
+ALGO_FLOPS_F64 = {"mimetic": 151.0, "direct": 330.0, "nnn": 729.0}
 FP64_PEAK_FLOPS = 1.25e12      # nominal dense FP64 rate of GB300 (152 SMs)
 L2_FLUSH_BYTES = 512 << 20
 MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this

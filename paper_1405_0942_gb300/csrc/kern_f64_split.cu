@@ -269,83 +269,96 @@ __global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   pass_B<S, LdRO>(a, st->cur, red);
 }
 
-// The next-nearest-neighbour current (section "Next Nearest Neighbor
-// Mimetic Approach") at interior node n and B there: in each index surface
-// r (spanned by p = r+1, q = r+2 mod 3) the loop through the eight in-plane
-// neighbours, counter-clockwise about +r from the corner +e_p - e_q, with
-// edge-mean B for the circulation (eq. "current discrete" with eight
-// contributions) and, for the vector area (eq. "sum of eight triangles"),
-// the four corner triangles (edges meeting at the corners, / 2) plus the
-// inner quadrilateral through the face neighbours (/ 4); the three areas
-// are the rows of M in eq. "current matrix equation", solved here by the
-// adjugate, J = (c_0 a_1 x a_2 + c_1 a_2 x a_0 + c_2 a_0 x a_1) / det M.
-// Positions are taken relative to the node: y (displacement) differences
-// plus the label offsets.
+// One octilateral loop of the next-nearest-neighbour current (section
+// "Next Nearest Neighbor Mimetic Approach") in the index surface spanned by
+// P and Q: the eight in-plane neighbours V_1..V_8 at (along P, along Q) =
+// (1,-1), (1,0), (1,1), (0,1), (-1,1), (-1,0), (-1,-1), (0,-1), positions
+// r_m taken relative to the node (displacement differences plus the label
+// offsets).  Returns twice the circulation and twice the vector area (the
+// common factor 1/2 cancels in M J = c):
+//   circulation with edge-mean B (eq. "current discrete", eight edges):
+//     sum_m (B_m + B_m+1)/2 . (r_m+1 - r_m) = sum_m B_m . (r_m+1 - r_m-1) / 2
+//   vector area (eq. "sum of eight triangles": four corner triangles plus the
+//   inner quadrilateral through V_2, V_4, V_6, V_8): a surface spanning the
+//   loop, so its vector area is the loop's, sum_m r_m x r_m+1 / 2.
+// The vertices stream through registers (three positions and one B live).
+template <int P, int Q, class LD>
+__device__ __forceinline__ void nnn_loop(const SplitArgs& a, const double* __restrict__ y,
+                                         int N, int n, const double yc[3], double& circ2,
+                                         double area2[3]) {
+  constexpr int OP[8] = {1, 1, 1, 0, -1, -1, -1, 0};
+  constexpr int OQ[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
+  const int sp = P == 0 ? 1 : (P == 1 ? a.nx : a.nx * a.ny);
+  const int sq = Q == 0 ? 1 : (Q == 1 ? a.nx : a.nx * a.ny);
+  const double hp = 0.5 * a.h2[P], hq = 0.5 * a.h2[Q];
+  double r0[3], b0[3], r1[3], rp[3], rc[3], bc[3];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int nn = n + OP[m] * sp + OQ[m] * sq;
+    double rv[3], bv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rv[c] = LD::ld(&y[c * N + nn]) - yc[c];
+      bv[c] = LD::ld(&a.Bb[c * N + nn]);
+    }
+    if (OP[m] != 0) rv[P] += OP[m] > 0 ? hp : -hp;
+    if (OQ[m] != 0) rv[Q] += OQ[m] > 0 ? hq : -hq;
+    if (m == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { r0[c] = rv[c]; b0[c] = bv[c]; }
+    } else {
+      // r_m-1 x r_m
+      const double* u = m == 1 ? r0 : rc;
+      if (m == 1) {
+        area2[0] = u[1] * rv[2] - u[2] * rv[1];
+        area2[1] = u[2] * rv[0] - u[0] * rv[2];
+        area2[2] = u[0] * rv[1] - u[1] * rv[0];
+      } else {
+        area2[0] = fma(u[1], rv[2], fma(-u[2], rv[1], area2[0]));
+        area2[1] = fma(u[2], rv[0], fma(-u[0], rv[2], area2[1]));
+        area2[2] = fma(u[0], rv[1], fma(-u[1], rv[0], area2[2]));
+      }
+      if (m >= 2) {  // the term of vertex m-1: B_m-1 . (r_m - r_m-2)
+        const double* w = m == 2 ? r0 : rp;
+        double t = bc[0] * (rv[0] - w[0]);
+        t = fma(bc[1], rv[1] - w[1], t);
+        t = fma(bc[2], rv[2] - w[2], t);
+        circ2 = m == 2 ? t : circ2 + t;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (m == 1) r1[c] = rv[c];
+        rp[c] = m == 1 ? r0[c] : rc[c];
+        rc[c] = rv[c];
+        bc[c] = bv[c];
+      }
+    }
+  }
+  // close the loop: r_8 x r_1, and the terms of V_8 and V_1
+  area2[0] = fma(rc[1], r0[2], fma(-rc[2], r0[1], area2[0]));
+  area2[1] = fma(rc[2], r0[0], fma(-rc[0], r0[2], area2[1]));
+  area2[2] = fma(rc[0], r0[1], fma(-rc[1], r0[0], area2[2]));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) circ2 = fma(bc[c], r0[c] - rp[c], circ2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) circ2 = fma(b0[c], r1[c] - rc[c], circ2);
+}
+
+// The next-nearest-neighbour current at interior node n and B there: the
+// three loops (surfaces r = 0, 1, 2 spanned by p = r+1, q = r+2 mod 3,
+// counter-clockwise about +r) give the rows of M and the entries of c in
+// eq. "current matrix equation", solved by the adjugate,
+// J = (c_0 a_1 x a_2 + c_1 a_2 x a_0 + c_2 a_0 x a_1) / det M.
 template <class LD>
 __device__ __forceinline__ void nnn_current(const SplitArgs& a, const double* __restrict__ y,
                                             int N, int n, double J[3], double B[3]) {
-  const int st[3] = {1, a.nx, a.nx * a.ny};
   double yc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) yc[c] = LD::ld(&y[c * N + n]);
   double M[3][3], cr[3];
-#pragma unroll 1
-  for (int r = 0; r < 3; ++r) {
-    const int p = (r + 1) % 3, q = (r + 2) % 3;
-    // vertex offsets (along p, along q) of V1 .. V8
-    const int op[8] = {1, 1, 1, 0, -1, -1, -1, 0};
-    const int oq[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
-    double xv[8][3], Bv[8][3];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int nn = n + op[m] * st[p] + oq[m] * st[q];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        xv[m][c] = LD::ld(&y[c * N + nn]) - yc[c];
-        Bv[m][c] = LD::ld(&a.Bb[c * N + nn]);
-      }
-      xv[m][p] += 0.5 * op[m] * a.h2[p];
-      xv[m][q] += 0.5 * oq[m] * a.h2[q];
-    }
-    double circ = 0.0, dx[8][3];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int m1 = (m + 1) & 7;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dx[m][c] = xv[m1][c] - xv[m][c];
-        circ = fma(0.5 * (Bv[m][c] + Bv[m1][c]), dx[m][c], circ);
-      }
-    }
-    double area[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {  // corner triangles: (dx_2, dx_3), ..., (dx_8, dx_1)
-      const double* e0 = dx[2 * t + 1];
-      const double* e1 = dx[(2 * t + 2) & 7];
-      area[0] += 0.5 * (e0[1] * e1[2] - e0[2] * e1[1]);
-      area[1] += 0.5 * (e0[2] * e1[0] - e0[0] * e1[2]);
-      area[2] += 0.5 * (e0[0] * e1[1] - e0[1] * e1[0]);
-    }
-    double qd[4][3];  // inner quadrilateral V2 -> V4 -> V6 -> V8
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      qd[0][c] = xv[3][c] - xv[1][c];
-      qd[1][c] = xv[5][c] - xv[3][c];
-      qd[2][c] = xv[7][c] - xv[5][c];
-      qd[3][c] = xv[1][c] - xv[7][c];
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const double* e0 = qd[t];
-      const double* e1 = qd[(t + 1) & 3];
-      area[0] += 0.25 * (e0[1] * e1[2] - e0[2] * e1[1]);
-      area[1] += 0.25 * (e0[2] * e1[0] - e0[0] * e1[2]);
-      area[2] += 0.25 * (e0[0] * e1[1] - e0[1] * e1[0]);
-    }
-    cr[r] = circ;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) M[r][c] = area[c];
-  }
+  nnn_loop<1, 2, LD>(a, y, N, n, yc, cr[0], M[0]);
+  nnn_loop<2, 0, LD>(a, y, N, n, yc, cr[1], M[1]);
+  nnn_loop<0, 1, LD>(a, y, N, n, yc, cr[2], M[2]);
   double adj[3][3];  // adj[r] = a_{r+1} x a_{r+2}
 #pragma unroll
   for (int r = 0; r < 3; ++r) {

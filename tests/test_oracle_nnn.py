@@ -125,3 +125,30 @@ def test_nnn_velocity_at_matches_the_field():
         un, rc = ora.velocity_at(g, x, B0, i, j, k, ora.NNN)
         assert rc == ora.OK
         assert np.abs(un - u[:, k, j, i]).max() <= 1e-14 * max(1.0, np.abs(u).max())
+
+
+def test_octilateral_area_and_circulation_depend_on_the_loop_only():
+    """The form the GPU pass evaluates: for any eight vertices (not planar),
+    the paper's area decomposition -- the four corner triangles (edges
+    meeting at V_2k+1 .. V_2k+3, / 2) plus the inner quadrilateral through
+    V_2, V_4, V_6, V_8 (/ 4) -- is the vector area of the closed loop,
+    1/2 sum_m r_m x r_m+1, whatever the origin; and the edge-mean
+    circulation sum_m (B_m + B_m+1)/2 . (r_m+1 - r_m) equals
+    sum_m B_m . (r_m+1 - r_m-1) / 2.  A dropped triangle, a wrong weight on
+    the quadrilateral or a shifted B index fails it."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        r = rng.normal(size=(8, 3)) + rng.normal(size=3)
+        B = rng.normal(size=(8, 3))
+        dx = np.roll(r, -1, axis=0) - r                      # dx_m = r_m+1 - r_m
+        corners = sum(np.cross(dx[2 * t + 1], dx[(2 * t + 2) % 8]) for t in range(4)) / 2
+        quad = r[[3, 5, 7, 1]] - r[[1, 3, 5, 7]]             # V2->V4->V6->V8->V2
+        inner = sum(np.cross(quad[t], quad[(t + 1) % 4]) for t in range(4)) / 4
+        loop = sum(np.cross(r[m], r[(m + 1) % 8]) for m in range(8)) / 2
+        assert np.allclose(corners + inner, loop, rtol=0, atol=1e-12 * np.abs(r).max() ** 2)
+        shifted = r - rng.normal(size=3)
+        loop2 = sum(np.cross(shifted[m], shifted[(m + 1) % 8]) for m in range(8)) / 2
+        assert np.allclose(loop2, loop, rtol=0, atol=1e-11 * np.abs(r).max() ** 2)
+        edge = sum((B[m] + B[(m + 1) % 8]) @ dx[m] for m in range(8)) / 2
+        vert = sum(B[m] @ (r[(m + 1) % 8] - r[m - 1]) for m in range(8)) / 2
+        assert abs(edge - vert) <= 1e-12 * np.abs(B).max() * np.abs(r).max()
