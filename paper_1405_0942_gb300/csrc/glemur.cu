@@ -276,32 +276,37 @@ void host_cta_range(long long n, int b, int G, long long& begin, long long& end)
 }
 
 // Plane of boundary item t, in the order of the kernels' boundary_node:
-// the z faces (whole planes), the y faces without their z edges, the x
-// faces without their y and z edges.
+// the inner parts of the z, y and x faces, the edges along x, y and z, the
+// corners.
 int host_boundary_plane(int nx, int ny, int nz, long long t) {
-  const long long fz = (long long)nx * ny, fy = (long long)nx * (nz - 2),
-                  fx = (long long)(ny - 2) * (nz - 2);
-  if (t < fz) return 0;
-  if (t < 2 * fz) return nz - 1;
+  const long long xi = nx - 2, yi = ny - 2, zi = nz - 2;
+  const long long fz = xi * yi, fy = xi * zi, fx = yi * zi;
+  if (t < 2 * fz) return t < fz ? 0 : nz - 1;
   t -= 2 * fz;
-  if (t < 2 * fy) return 1 + (int)((t < fy ? t : t - fy) / nx);
+  if (t < 2 * fy) return 1 + (int)((t < fy ? t : t - fy) / xi);
   t -= 2 * fy;
-  return 1 + (int)((t < fx ? t : t - fx) / (ny - 2));
+  if (t < 2 * fx) return 1 + (int)((t < fx ? t : t - fx) / yi);
+  t -= 2 * fx;
+  if (t < 4 * xi) return ((t / xi) & 2) ? nz - 1 : 0;
+  t -= 4 * xi;
+  if (t < 4 * yi) return ((t / yi) & 2) ? nz - 1 : 0;
+  t -= 4 * yi;
+  if (t < 4 * zi) return 1 + (int)(t % zi);
+  t -= 4 * zi;
+  return (t & 4) ? nz - 1 : 0;
 }
 
 // The persistent kernel's plan: per CTA the plane intervals of its pass-B
-// work (interior range, then the boundary range split at the face blocks)
-// and of its pass-C work (the interior range); per plane how many CTAs'
-// intervals contain it.  False if the plan does not fit.
+// work (the interior range, then the planes of its boundary range as runs
+// of adjacent planes, at most PERSIST_BI - 1 of them: the last run absorbs
+// any further planes, a superset that only widens the waits) and of its
+// pass-C work (the interior range); per plane how many CTAs' intervals
+// contain it.  False if the plan does not fit.
 bool persist_plan(glemur_ctx* c, int G) {
   const int nx = c->nx, ny = c->ny, nz = c->nz;
   if (G < 1 || G > PERSIST_MAX_CTAS) return false;
   const long long N = c->N, NI = (long long)(nx - 2) * (ny - 2) * (nz - 2);
   const long long A = (long long)(nx - 2) * (ny - 2);
-  const long long fz = (long long)nx * ny, fy = (long long)nx * (nz - 2),
-                  fx = (long long)(ny - 2) * (nz - 2);
-  const long long blk[7] = {0, fz, 2 * fz, 2 * fz + fy, 2 * fz + 2 * fy, 2 * fz + 2 * fy + fx,
-                            2 * fz + 2 * fy + 2 * fx};
   int* h = new (std::nothrow) int[4 * (size_t)nz + 64 + (size_t)G * (2 * PERSIST_BI + 2)];
   if (!h) return false;
   int* cnt = h;                 // cntB, cntC: zeroed per launch
@@ -328,11 +333,18 @@ bool persist_plan(glemur_ctx* c, int G) {
     }
     host_cta_range(N - NI, b, G, t0, t1);
     int q = 1;
-    for (int f = 0; f < 6 && q < PERSIST_BI; ++f) {
-      const long long u = t0 > blk[f] ? t0 : blk[f], v = t1 < blk[f + 1] ? t1 : blk[f + 1];
-      if (v <= u) continue;
-      vb[2 * q] = host_boundary_plane(nx, ny, nz, u);
-      vb[2 * q + 1] = host_boundary_plane(nx, ny, nz, v - 1);
+    for (long long t = t0; t < t1; ++t) {
+      const int pl = host_boundary_plane(nx, ny, nz, t);
+      if (q > 1) {
+        int& lo = vb[2 * (q - 1)];
+        int& hi = vb[2 * (q - 1) + 1];
+        if ((pl >= lo - 1 && pl <= hi + 1) || q == PERSIST_BI) {
+          lo = pl < lo ? pl : lo;
+          hi = pl > hi ? pl : hi;
+          continue;
+        }
+      }
+      vb[2 * q] = vb[2 * q + 1] = pl;
       ++q;
     }
     for (int qq = 0; qq < PERSIST_BI; ++qq)

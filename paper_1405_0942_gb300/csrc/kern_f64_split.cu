@@ -91,87 +91,95 @@ __device__ __forceinline__ int interior_node(const SplitArgs& a, int t, int& i, 
   return (k * a.ny + j) * a.nx + i;
 }
 
-// Boundary nodes enumerated densely, face by face: the two z faces (whole
-// planes), the two y faces without their z edges, the two x faces without
-// their y and z edges; b in [0, N - interior).
+// Boundary nodes enumerated densely, grouped so that the lanes of a warp
+// share one stencil variant per axis: the inner parts of the two z faces,
+// the two y faces and the two x faces (one boundary index coordinate), the
+// edges along x, y and z (two), then the eight corners; b in
+// [0, N - interior).  (A warp mixes variants only where it straddles two
+// groups.)  The host's persistent-kernel plan mirrors this order.
 __device__ __forceinline__ int boundary_node(const SplitArgs& a, int b, int& i, int& j, int& k) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int fz = nx * ny, fy = nx * (nz - 2);
+  const int xi = nx - 2, yi = ny - 2, zi = nz - 2;
+  const int fz = xi * yi, fy = xi * zi, fx = yi * zi;
   if (b < 2 * fz) {
     k = b < fz ? 0 : nz - 1;
     const int r = b < fz ? b : b - fz;
-    j = r / nx;
-    i = r - j * nx;
-  } else if (b < 2 * fz + 2 * fy) {
-    int r = b - 2 * fz;
-    j = r < fy ? 0 : ny - 1;
-    r = r < fy ? r : r - fy;
-    k = 1 + r / nx;
-    i = r % nx;
+    i = 1 + r % xi;
+    j = 1 + r / xi;
+  } else if ((b -= 2 * fz) < 2 * fy) {
+    j = b < fy ? 0 : ny - 1;
+    const int r = b < fy ? b : b - fy;
+    i = 1 + r % xi;
+    k = 1 + r / xi;
+  } else if ((b -= 2 * fy) < 2 * fx) {
+    i = b < fx ? 0 : nx - 1;
+    const int r = b < fx ? b : b - fx;
+    j = 1 + r % yi;
+    k = 1 + r / yi;
+  } else if ((b -= 2 * fx) < 4 * xi) {
+    const int e = b / xi;
+    i = 1 + b % xi;
+    j = (e & 1) ? ny - 1 : 0;
+    k = (e & 2) ? nz - 1 : 0;
+  } else if ((b -= 4 * xi) < 4 * yi) {
+    const int e = b / yi;
+    j = 1 + b % yi;
+    i = (e & 1) ? nx - 1 : 0;
+    k = (e & 2) ? nz - 1 : 0;
+  } else if ((b -= 4 * yi) < 4 * zi) {
+    const int e = b / zi;
+    k = 1 + b % zi;
+    i = (e & 1) ? nx - 1 : 0;
+    j = (e & 2) ? ny - 1 : 0;
   } else {
-    const int fx = (ny - 2) * (nz - 2);
-    int r = b - 2 * fz - 2 * fy;
-    i = r < fx ? 0 : nx - 1;
-    r = r < fx ? r : r - fx;
-    k = 1 + r / (ny - 2);
-    j = 1 + r % (ny - 2);
+    b -= 4 * zi;
+    i = (b & 1) ? nx - 1 : 0;
+    j = (b & 2) ? ny - 1 : 0;
+    k = (b & 4) ? nz - 1 : 0;
   }
   return (k * ny + j) * nx + i;
 }
 
-// Column a of G at node (i, j, k) from the stage input y.
-template <class LD>
-__device__ __forceinline__ void split_gcol(const SplitArgs& a, const double* __restrict__ y, int N,
-                                           int n, int ax, int idx, int ext, int stride,
-                                           double out[3]) {
-  const int kind = idx == 0 ? 1 : (idx == ext - 1 ? 2 : 0);
+// One column of G from the stage input y along an axis of node stride
+// `stride`, without the 2 h_a e_a term.  ONE = false: the central
+// difference v(n+s) - v(n-s).  ONE = true: the second-order one-sided
+// difference into the domain, (4 v(n+s) - 3 v(n)) - v(n+2s) at the low face
+// (sg = +1) and (3 v(n) - 4 v(n-s)) + v(n-2s) at the high face (sg = -1),
+// both as sg times the first form with s -> sg s: the signs ride on
+// constants chosen by a select (multiplying by -1 is exact), so both faces
+// run the same three FP64 instructions per component.
+template <bool ONE, class LD>
+__device__ __forceinline__ void gcol(const double* __restrict__ y, int N, int n, int stride,
+                                     int sg, double out[3]) {
+  const int s = sg * stride;
+  const double c4 = sg > 0 ? 4.0 : -4.0, m3 = sg > 0 ? -3.0 : 3.0, m1 = sg > 0 ? -1.0 : 1.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double* v = y + c * N;
-    double d;
-    if (kind == 0)
-      d = LD::ld(&v[n + stride]) - LD::ld(&v[n - stride]);
-    else if (kind == 1)
-      d = (4.0 * LD::ld(&v[n + stride]) - 3.0 * LD::ld(&v[n])) - LD::ld(&v[n + 2 * stride]);
+    if (!ONE)
+      out[c] = LD::ld(&v[n + stride]) - LD::ld(&v[n - stride]);
     else
-      d = (3.0 * LD::ld(&v[n]) - 4.0 * LD::ld(&v[n - stride])) + LD::ld(&v[n - 2 * stride]);
-    out[c] = d;
+      out[c] = fma(m1, LD::ld(&v[n + 2 * s]), fma(c4, LD::ld(&v[n + s]), m3 * LD::ld(&v[n])));
   }
-  out[ax] += a.h2[ax];
 }
 
-// B and 1/det G at node n = (i, j, k) from the stage input y (eq. "B
-// transformation"), stored at node nw (n itself, or a periodic ghost node
-// that carries n's B); returns the node's energy term zeta |B|^2 det G if
-// `energy`.  FACE: the general stencil (one-sided differences on the
-// boundary faces the node touches), else central differences only.
-template <bool FACE, class LD = LdRO>
-__device__ __forceinline__ double split_B_node(const SplitArgs& a, const double* __restrict__ y,
-                                               int N, int n, int i, int j, int k, bool state,
-                                               bool energy, int nw) {
-  double g0[3], g1[3], g2[3];
-  if (FACE) {
-    split_gcol<LD>(a, y, N, n, 0, i, a.nx, 1, g0);
-    split_gcol<LD>(a, y, N, n, 1, j, a.ny, a.nx, g1);
-    split_gcol<LD>(a, y, N, n, 2, k, a.nz, a.nx * a.ny, g2);
-  } else {
-    const int sy = a.nx, sz = a.nx * a.ny;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double* v = y + c * N;
-      g0[c] = LD::ld(&v[n + 1]) - LD::ld(&v[n - 1]);
-      g1[c] = LD::ld(&v[n + sy]) - LD::ld(&v[n - sy]);
-      g2[c] = LD::ld(&v[n + sz]) - LD::ld(&v[n - sz]);
-    }
-    g0[0] += a.h2[0];
-    g1[1] += a.h2[1];
-    g2[2] += a.h2[2];
-  }
+// det G, 1/det G and B = G B0s / det G at node n from its columns (eq. "B
+// transformation"); B (and 1/det G if rb is set) stored at node nw (n
+// itself, or a periodic ghost node that carries n's B), with G: the
+// differences and 1/det G interleaved for pass C (interior nodes).  Returns
+// the node's energy term zeta |B|^2 det G if `energy`.
+template <bool WITH_G>
+__device__ __forceinline__ double split_B_finish(const SplitArgs& a, int N, int n, int i, int j,
+                                                 int k, bool state, bool energy, int nw,
+                                                 double g0[3], double g1[3], double g2[3]) {
+  g0[0] += a.h2[0];
+  g1[1] += a.h2[1];
+  g2[2] += a.h2[2];
   const double det = det3(g0, g1, g2);
   if (le_zero(det))  // NaN: reported by the error norm
     atomicOr(&a.st->flags, state ? FLAG_COLLAPSED : FLAG_FOLDED_TRIAL);
   const double r = recip(det);
-  if (!FACE) {
+  if (WITH_G) {
     // the node's differences and 1/det G for pass C, as five 16-byte
     // stores (10 N doubles: size_t offsets)
     double2* q = reinterpret_cast<double2*>(a.Gb + (size_t)n * 10);
@@ -194,6 +202,55 @@ __device__ __forceinline__ double split_B_node(const SplitArgs& a, const double*
   const int nb = (i == 0 || i == a.nx - 1) + (j == 0 || j == a.ny - 1) + (k == 0 || k == a.nz - 1);
   const double zeta = nb == 0 ? 1.0 : nb == 1 ? 0.5 : nb == 2 ? 0.25 : 0.125;
   return zeta * dot3(B, B) * det;
+}
+
+// B at an interior node (central differences), storing G for pass C.
+template <class LD>
+__device__ __forceinline__ double split_B_interior(const SplitArgs& a,
+                                                   const double* __restrict__ y, int N, int n,
+                                                   int i, int j, int k, bool state,
+                                                   bool energy) {
+  double g0[3], g1[3], g2[3];
+  gcol<false, LD>(y, N, n, 1, 1, g0);
+  gcol<false, LD>(y, N, n, a.nx, 1, g1);
+  gcol<false, LD>(y, N, n, a.nx * a.ny, 1, g2);
+  return split_B_finish<true>(a, N, n, i, j, k, state, energy, n, g0, g1, g2);
+}
+
+// B at a boundary node (or, with periodic z, at the partner of a ghost
+// node): one-sided along the axes with sx, sy, sz != 0 (+1 low face, -1
+// high face), central along the others; the variant is a template
+// argument, so each runs its own FP64 instructions only.
+template <bool OX, bool OY, bool OZ, class LD>
+__device__ __forceinline__ double split_B_bvar(const SplitArgs& a, const double* __restrict__ y,
+                                               int N, int n, int i, int j, int k, int sx,
+                                               int sy, int sz, bool state, bool energy,
+                                               int nw) {
+  double g0[3], g1[3], g2[3];
+  gcol<OX, LD>(y, N, n, 1, sx, g0);
+  gcol<OY, LD>(y, N, n, a.nx, sy, g1);
+  gcol<OZ, LD>(y, N, n, a.nx * a.ny, sz, g2);
+  return split_B_finish<false>(a, N, n, i, j, k, state, energy, nw, g0, g1, g2);
+}
+
+template <class LD>
+__device__ __forceinline__ double split_B_boundary(const SplitArgs& a,
+                                                   const double* __restrict__ y, int N, int n,
+                                                   int i, int j, int k, int sx, int sy, int sz,
+                                                   bool state, bool energy, int nw) {
+#define GLEMUR_BVAR(X, Y, Z) \
+  return split_B_bvar<X, Y, Z, LD>(a, y, N, n, i, j, k, sx, sy, sz, state, energy, nw)
+  switch ((sx != 0) * 4 + (sy != 0) * 2 + (sz != 0)) {
+    case 0: GLEMUR_BVAR(false, false, false);
+    case 1: GLEMUR_BVAR(false, false, true);
+    case 2: GLEMUR_BVAR(false, true, false);
+    case 3: GLEMUR_BVAR(false, true, true);
+    case 4: GLEMUR_BVAR(true, false, false);
+    case 5: GLEMUR_BVAR(true, false, true);
+    case 6: GLEMUR_BVAR(true, true, false);
+    default: GLEMUR_BVAR(true, true, true);
+  }
+#undef GLEMUR_BVAR
 }
 
 // This CTA's partial of kind `kind`; the slots of the partial stride beyond
@@ -237,20 +294,23 @@ __device__ __forceinline__ void pass_B(const SplitArgs& a, int cur, double* red)
   for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
     int i, j, k;
     const int n = interior_node(a, t, i, j, k);
-    eacc += split_B_node<false, LD>(a, y, N, n, i, j, k, S == 0, energy, n);
+    eacc += split_B_interior<LD>(a, y, N, n, i, j, k, S == 0, energy);
   }
   cta_range(N - NI, tb, te);
   for (int b = tb + threadIdx.x; b < te; b += blockDim.x) {
     int i, j, k;
     const int n = boundary_node(a, b, i, j, k);
-    if (a.periodic && (k == 0 || k == a.nz - 1)) {
+    const int sx = i == 0 ? 1 : (i == a.nx - 1 ? -1 : 0);
+    const int sy = j == 0 ? 1 : (j == a.ny - 1 ? -1 : 0);
+    const int sz = k == 0 ? 1 : (k == a.nz - 1 ? -1 : 0);
+    if (a.periodic && sz != 0) {
       // a ghost plane carries its partner's B (section "Boundary
       // Conditions"); it is not part of the period's energy
-      const int kk = k == 0 ? a.nz - 2 : 1;
+      const int kk = sz > 0 ? a.nz - 2 : 1;
       const int np = (kk * a.ny + j) * a.nx + i;
-      split_B_node<true, LD>(a, y, N, np, i, j, kk, S == 0, false, n);
+      split_B_boundary<LD>(a, y, N, np, i, j, kk, sx, sy, 0, S == 0, false, n);
     } else {
-      eacc += split_B_node<true, LD>(a, y, N, n, i, j, k, S == 0, energy, n);
+      eacc += split_B_boundary<LD>(a, y, N, n, i, j, k, sx, sy, sz, S == 0, energy, n);
     }
   }
   pdl_trigger();
@@ -261,7 +321,7 @@ __device__ __forceinline__ void pass_B(const SplitArgs& a, int cur, double* red)
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
+__global__ void __launch_bounds__(256, 4) k_split_B(const SplitArgs a) {
   pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
