@@ -57,11 +57,13 @@ MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # captured from (kernel_source_hash()); a workload without an entry, or one
 # whose kernels have changed since, reports null
 NCU_TRAFFIC = {
-    ("braid64", "fp64", "mimetic"): (58536491, "795a5dc3b9f8"),
-    ("braid64", "fp64", "direct"): (31328981, "795a5dc3b9f8"),
-    ("braid64", "mixed", "mimetic"): (15707221, "795a5dc3b9f8"),
-    ("braid64", "mixed", "direct"): (15825451, "795a5dc3b9f8"),
-    ("braid128", "mixed", "mimetic"): (155372715, "795a5dc3b9f8"),
+    ("braid64", "fp64", "mimetic"): (58666027, "8f6eb70c2a78"),
+    ("braid64", "fp64", "direct"): (31328981, "8f6eb70c2a78"),
+    ("braid64", "fp64", "nnn"): (44237867, "8f6eb70c2a78"),
+    ("periodic64", "fp64", "mimetic"): (58451968, "8f6eb70c2a78"),
+    ("braid64", "mixed", "mimetic"): (15706709, "8f6eb70c2a78"),
+    ("braid64", "mixed", "direct"): (15825109, "8f6eb70c2a78"),
+    ("braid128", "mixed", "mimetic"): (155344939, "8f6eb70c2a78"),
 }
 
 
