@@ -389,6 +389,12 @@ def roofline_entry(whole, split, w, name, precision, curl, hbm_peak, peak_kind):
 # stage input, B0 and the adjoint of k_s, write the adjoint of the stage
 # input, read and write the B0 adjoint (6 FP64 vectors)
 ADJ_ALGO_BYTES = 6 * 24.0
+# FP64 flops per interior node-stage of the reverse step (FMA = 2): the
+# stage recompute 151, the reverse of u = J x B and of the current with the
+# current formed again 203, the pull-back reverse with the gathered B
+# adjoint 137, the stage-input adjoint gather 18, the reverse Runge-Kutta
+# combine 18 (3 + 6 s over the stages' s = 0..5, averaged)
+ADJ_ALGO_FLOPS = 527.0
 
 
 def adjoint_measure(G, torch, w, precision, steps, flush, hbm_peak, peak_kind):
@@ -422,11 +428,18 @@ def adjoint_measure(G, torch, w, precision, steps, flush, hbm_peak, peak_kind):
     ms = float(np.mean(times))
     I = g.n_interior
     gbs = ADJ_ALGO_BYTES * I * 6 / (ms * 1e-3) / 1e9
+    tf = ADJ_ALGO_FLOPS * I * 6 / (ms * 1e-3) / 1e12
+    # the reverse kernels run FP64 arithmetic on either storage precision:
+    # bound by the FP64 pipe, like the forward FP64 passes
     return {"value": I * 6 / (ms * 1e-3), "unit": "node-stage VJPs/s", "ms_per_step": ms,
             "precision": precision,
             "step": "glemur_vjp_step: six-stage recompute + reverse combine + six stage VJPs",
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_FLOPS / 1e12,
+                         "unit": "TFLOP/s", "frac": tf * 1e12 / FP64_PEAK_FLOPS,
+                         "peak_kind": "nominal FP64 rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                         "algorithmic_flops_per_node_stage": ADJ_ALGO_FLOPS,
+                         "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                         "hbm_peak_kind": peak_kind,
                          "algorithmic_bytes_per_node_stage": ADJ_ALGO_BYTES}}
 
 
