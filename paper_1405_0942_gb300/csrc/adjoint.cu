@@ -19,7 +19,8 @@
 //      interior neighbours, reverse the pull-back -> adjoint of g_a, mu;
 //   3. at every node, gather the adjoint of y from the g_a adjoints of the
 //      nodes whose difference stencils contain it (central inside, one-sided
-//      on boundary faces).
+//      on boundary faces); in the reverse step the same kernel applies the
+//      Runge-Kutta combine (lam, lam_k_j) to it directly.
 // Boundary nodes are line-tied: their position adjoint is not propagated.
 // Every kernel here is launched as a programmatic dependent of the one
 // before it (launch_pdl) and starts with pdl_wait(), before any memory
@@ -405,13 +406,12 @@ __device__ __forceinline__ double gcoef(int m, int p, int n) {
 // Adjoint of the stage input at interior node n = (i, j, k), general
 // form: the g_a adjoints of every stencil (central or one-sided) that
 // contains the node.
-__device__ __forceinline__ void positions_general(const AdjGeom& g, const double* lamg,
-                                                  double* lam_y, int N, int n, int i, int j,
-                                                  int k) {
+__device__ __forceinline__ void positions_general(const AdjGeom& g, const double* lamg, int N,
+                                                  int n, int i, int j, int k, double ly[3]) {
   const int st[3] = {1, g.nx, g.nx * g.ny};
   const int id[3] = {i, j, k};
   const int ext[3] = {g.nx, g.ny, g.nz};
-  double ly[3] = {0, 0, 0};
+  ly[0] = ly[1] = ly[2] = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int dm = -2; dm <= 2; ++dm) {
       const int m = id[a] + dm;
@@ -421,18 +421,44 @@ __device__ __forceinline__ void positions_general(const AdjGeom& g, const double
       const int nm = n + dm * st[a];
       for (int c = 0; c < 3; ++c) ly[c] += w * lamg[(a * 3 + c) * N + nm];
     }
-  for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+}
+
+// Where the stage-input adjoint ly of interior node n goes.  S < 0: into
+// lam_y.  S = 0..5: straight into the reverse Runge-Kutta combine after
+// stage S (lam += ly, lam_k_j += dt a_Sj ly for j < S), with no round trip
+// through lam_y.
+template <int S>
+__device__ __forceinline__ void positions_out(int N, int n, const double ly[3], double* lam_y,
+                                              const double* cj, double* lam,
+                                              double* const* lam_k) {
+  if constexpr (S < 0) {
+    for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int q = c * N + n;
+      lam[q] += ly[c];
+#pragma unroll
+      for (int j = 0; j < S; ++j) lam_k[j][q] += cj[j] * ly[c];
+    }
+  }
 }
 
 // Step 3: adjoint of the stage input at interior nodes (0 on the boundary).
 // Nodes at least 3 from every face are touched by central stencils only:
 // lam_y = sum_a lamg_a(n - e_a) - lamg_a(n + e_a); the shell between them
-// and the faces takes the general form.
-__global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
-  pdl_wait();
-  pdl_trigger();
+// and the faces takes the general form.  S >= 0: combined with the reverse
+// Runge-Kutta step of stage S (positions_out); boundary nodes then add
+// nothing (line-tied: their adjoint is 0).
+template <int S>
+__device__ __forceinline__ void adj_positions_s(const AdjGeom& g, const double* lamg,
+                                                double* lam_y, double dt, double* lam,
+                                                double* const* lam_k) {
   const int N = g.nx * g.ny * g.nz, NI = (g.nx - 2) * (g.ny - 2) * (g.nz - 2);
   const int st[3] = {1, g.nx, g.nx * g.ny};
+  double cj[S > 0 ? S : 1];
+#pragma unroll
+  for (int j = 0; j < (S > 0 ? S : 0); ++j) cj[j] = dt * AD_A[S][j];
   if (has_deep(g)) {
     const int ND = (g.nx - 6) * (g.ny - 6) * (g.nz - 6);
     GRID_LOOP(t, ND) {
@@ -442,54 +468,47 @@ __global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y) {
       for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c)
           ly[c] += lamg[(a * 3 + c) * N + n - st[a]] - lamg[(a * 3 + c) * N + n + st[a]];
-      for (int c = 0; c < 3; ++c) lam_y[c * N + n] = ly[c];
+      positions_out<S>(N, n, ly, lam_y, cj, lam, lam_k);
     }
     GRID_LOOP(sidx, NI - ND) {
       int i, j, k;
       const int n = adj_shell(g, sidx, i, j, k);
-      positions_general(g, lamg, lam_y, N, n, i, j, k);
+      double ly[3];
+      positions_general(g, lamg, N, n, i, j, k, ly);
+      positions_out<S>(N, n, ly, lam_y, cj, lam, lam_k);
     }
   } else {
     GRID_LOOP(t, NI) {
       int i, j, k;
       const int n = adj_interior(g, t, i, j, k);
-      positions_general(g, lamg, lam_y, N, n, i, j, k);
+      double ly[3];
+      positions_general(g, lamg, N, n, i, j, k, ly);
+      positions_out<S>(N, n, ly, lam_y, cj, lam, lam_k);
     }
   }
-  GRID_LOOP(b, N - NI) {  // line-tied: no position adjoint
-    int i, j, k;
-    const int n = adj_boundary(g, b, i, j, k);
-    for (int c = 0; c < 3; ++c) lam_y[c * N + n] = 0.0;
+  if constexpr (S < 0) {
+    GRID_LOOP(b, N - NI) {  // line-tied: no position adjoint
+      int i, j, k;
+      const int n = adj_boundary(g, b, i, j, k);
+      for (int c = 0; c < 3; ++c) lam_y[c * N + n] = 0.0;
+    }
   }
 }
 
-// Reverse Runge-Kutta combine after stage s: lam += lam_y,
-// lam_k_j += dt a_sj lam_y (j < s).
-template <int S>
-__device__ __forceinline__ void adj_rk_s(int N3, const double* lam_y, double dt, double* lam,
-                                         double* const* lam_k) {
-  double c[S > 0 ? S : 1];
-#pragma unroll
-  for (int j = 0; j < S; ++j) c[j] = dt * AD_A[S][j];
-  NODE_LOOP(N3) {
-    const double v = lam_y[n];
-    lam[n] += v;
-#pragma unroll
-    for (int j = 0; j < S; ++j) lam_k[j][n] += c[j] * v;
-  }
-}
-
-__global__ void k_adj_rk(int N3, const double* lam_y, int s, double dt, double* lam,
-                         double* const* lam_k) {
+// s < 0: the stage-input adjoint into lam_y; s = 0..5: combined with the
+// reverse Runge-Kutta step of stage s.
+__global__ void k_adj_positions(AdjGeom g, const double* lamg, double* lam_y, int s, double dt,
+                                double* lam, double* const* lam_k) {
   pdl_wait();
   pdl_trigger();
   switch (s) {  // stage-uniform: the loop over j unrolls without predicates
-    case 0: adj_rk_s<0>(N3, lam_y, dt, lam, lam_k); break;
-    case 1: adj_rk_s<1>(N3, lam_y, dt, lam, lam_k); break;
-    case 2: adj_rk_s<2>(N3, lam_y, dt, lam, lam_k); break;
-    case 3: adj_rk_s<3>(N3, lam_y, dt, lam, lam_k); break;
-    case 4: adj_rk_s<4>(N3, lam_y, dt, lam, lam_k); break;
-    default: adj_rk_s<5>(N3, lam_y, dt, lam, lam_k); break;
+    case 0: adj_positions_s<0>(g, lamg, lam_y, dt, lam, lam_k); break;
+    case 1: adj_positions_s<1>(g, lamg, lam_y, dt, lam, lam_k); break;
+    case 2: adj_positions_s<2>(g, lamg, lam_y, dt, lam, lam_k); break;
+    case 3: adj_positions_s<3>(g, lamg, lam_y, dt, lam, lam_k); break;
+    case 4: adj_positions_s<4>(g, lamg, lam_y, dt, lam, lam_k); break;
+    case 5: adj_positions_s<5>(g, lamg, lam_y, dt, lam, lam_k); break;
+    default: adj_positions_s<-1>(g, lamg, lam_y, dt, lam, lam_k); break;
   }
 }
 
@@ -741,10 +760,13 @@ __global__ void k_adj_seed_boundary(AdjGeom g, const double* d, YSave ys) {
 }
 
 // The stage VJP at the stage input y (B and 1/det G in Bb, rb; formed here
-// when form_B): lam_u -> lam_y, mu +=.
+// when form_B): lam_u -> lam_y, mu +=.  rk_s >= 0: the stage-input adjoint
+// goes straight into the reverse Runge-Kutta combine of stage rk_s (lam,
+// lam_k) instead of lam_y.
 template <typename T>
 void stage_vjp(const Adj& A, const double* y, double* Bb, double* rb, bool form_B,
-               const double* lam_u, const double* extra_lamB, double wE) {
+               const double* lam_u, const double* extra_lamB, double wE, int rk_s = -1,
+               double dt = 0.0, double* lam = nullptr, double* const* lam_k = nullptr) {
   const int N = A.N;
   if (form_B) launch_pdl(k_adj_fwd_B<T>, dim3(nblk(N)), dim3(256), 0, A.s, A.g, y, (const T*)A.B0s,
                          Bb, rb);
@@ -761,7 +783,8 @@ void stage_vjp(const Adj& A, const double* y, double* Bb, double* rb, bool form_
                              A.P(A.L.lamB));
   launch_pdl(k_adj_pullback<T>, dim3(nblk(N)), dim3(256), 0, A.s, A.g, y, (const T*)A.B0s, rb,
              A.P(A.L.lamP), A.P(A.L.lamg), A.P(A.L.lamr), A.P(A.L.lamB), wE, A.P(A.L.mu));
-  launch_pdl(k_adj_positions, dim3(nblk(N)), dim3(256), 0, A.s, A.g, A.P(A.L.lamg), A.P(A.L.lamy));
+  launch_pdl(k_adj_positions, dim3(nblk(N)), dim3(256), 0, A.s, A.g, (const double*)A.P(A.L.lamg),
+             A.P(A.L.lamy), rk_s, dt, lam, lam_k);
 }
 
 template <typename T>
@@ -803,13 +826,13 @@ int vjp_step_t(glemur_ctx* c, const Adj& A, double dt, const double* lam_next, d
   for (int s = 5; s >= 0; --s) {
     if (saved) {
       stage_vjp<T>(A, s == 0 ? (const double*)A.d : yS[s], BS[s], RS[s], false, lamk_h[s],
-                   nullptr, 0.0);
+                   nullptr, 0.0, s, dt, lam, lamk_d);
     } else {
       launch_pdl(k_adj_stage_input<T>, dim3(nblk(N3)), dim3(256), 0, A.s, N3, (const T*)A.d, kp_d,
                  s, dt, A.P(A.L.y));
-      stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, lamk_h[s], nullptr, 0.0);
+      stage_vjp<T>(A, A.P(A.L.y), A.P(A.L.Bb), A.P(A.L.rb), true, lamk_h[s], nullptr, 0.0, s,
+                   dt, lam, lamk_d);
     }
-    launch_pdl(k_adj_rk, dim3(nblk(N3)), dim3(256), 0, A.s, N3, A.P(A.L.lamy), s, dt, lam, lamk_d);
   }
   launch_pdl(k_adj_mu_out, dim3(nblk(A.N)), dim3(256), 0, A.s, A.g, A.P(A.L.mu), mu_B0);
   e = cudaGetLastError();
