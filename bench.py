@@ -14,7 +14,7 @@ been timed (so that the clock sampler sees the load); `value` and
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 (torchrun, one rank per GPU): every rank relaxes its own copy of the
-workload (replicas; the step has no cross-GPU exchange in this build) and
+workload (replicas: no data crosses between GPUs) and
 `value` is the sum over ranks divided by the slowest rank's time.
 """
 from __future__ import annotations
