@@ -348,6 +348,32 @@ int glemur_vjp_step(glemur_ctx* ctx, double dt, const double* lam_next, double* 
 int glemur_loss_grad(glemur_ctx* ctx, int loss, double* value, double* lam, double* mu_B0,
                      void* adj_ws, size_t adj_bytes);
 
+/* Device bytes of the segment workspace glemur_adjoint_segment needs for
+ * n_steps steps with a checkpoint every `every` steps: ceil(n_steps/every)
+ * state checkpoints, the states of one segment (min(n_steps, every)) and
+ * one adjoint field, each rounded up to 256 bytes (0 for invalid
+ * arguments). */
+size_t glemur_adjoint_segment_bytes(glemur_ctx* ctx, int n_steps, int every);
+
+/* The reverse pass over a recorded segment, natively: the loss (as in
+ * glemur_loss_grad) of the state reached from the positions x0 by n_steps
+ * fixed steps of the sizes dts[0..n_steps-1] (host array; the schedule a
+ * controlled run recorded, glemur_get_dt_schedule), into *value, and its
+ * gradients: with respect to x0 into lam_x0 and with respect to B0 into
+ * mu_B0 (device float64 fields, overwritten).  Forward: glemur_set_x(x0),
+ * then the steps, keeping the raw state every `every` steps in seg_ws;
+ * backward: each segment recomputed forwards from its checkpoint with its
+ * states kept, the loss gradient seeded at the final state, and the steps'
+ * glemur_vjp_step in reverse -- checkpointing with recompute, memory
+ * O(n_steps/every + every) states.  x0 must not alias the workspaces;
+ * seg_ws (256-byte aligned, glemur_adjoint_segment_bytes) and adj_ws (as
+ * for glemur_vjp_step) are caller-owned.  Leaves the context at state x0
+ * and synchronises its stream.  Errors: BADARG, WORKSPACE, CUDA and those
+ * of the steps (e.g. COLLAPSED). */
+int glemur_adjoint_segment(glemur_ctx* ctx, const double* x0, const double* dts, int n_steps,
+                           int every, int loss, double* value, double* lam_x0, double* mu_B0,
+                           void* adj_ws, size_t adj_bytes, void* seg_ws, size_t seg_bytes);
+
 /* out[p] = sum_m dB0[p*m_len + m] * mu[m] for p < n_params (device arrays):
  * the gradient with respect to parameters theta of B0(theta) from the
  * field adjoint mu_B0 and dB0/dtheta.  Asynchronous on `stream`. */

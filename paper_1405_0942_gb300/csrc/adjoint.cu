@@ -914,6 +914,90 @@ int glemur_loss_grad(glemur_ctx* c, int loss, double* value, double* lam, double
                                      : loss_grad_t<double>(c, A, loss, value, lam, mu_B0);
 }
 
+size_t glemur_adjoint_segment_bytes(glemur_ctx* c, int n_steps, int every) {
+  if (!c || n_steps < 0 || every < 1) return 0;
+  int nx, ny, nz, prec;
+  double h[3];
+  void *d, *B0s, *k[5], *stream;
+  if (ctx_info(c, &nx, &ny, &nz, h, &prec, &d, &B0s, k, &stream)) return 0;
+  const size_t S = (glemur_state_bytes(c) + 255) & ~(size_t)255;
+  const size_t F = (sizeof(double) * 3 * (size_t)nx * ny * nz + 255) & ~(size_t)255;
+  const size_t nseg = n_steps > 0 ? ((size_t)n_steps + every - 1) / every : 1;
+  const size_t per = (size_t)(n_steps < every ? n_steps : every);
+  return (nseg + per) * S + F;
+}
+
+int glemur_adjoint_segment(glemur_ctx* c, const double* x0, const double* dts, int n, int every,
+                           int loss, double* value, double* lam_x0, double* mu_B0, void* adj_ws,
+                           size_t adj_bytes, void* seg_ws, size_t seg_bytes) {
+  if (!c || !x0 || !value || !lam_x0 || !mu_B0 || n < 0 || every < 1 || (n > 0 && !dts) ||
+      (loss != GLEMUR_LOSS_ENERGY && loss != GLEMUR_LOSS_XI))
+    return GLEMUR_ERR_BADARG;
+  for (int i = 0; i < n; ++i)
+    if (!(dts[i] > 0) || !std::isfinite(dts[i])) return GLEMUR_ERR_BADARG;
+  const size_t need = glemur_adjoint_segment_bytes(c, n, every);
+  if (!need || !seg_ws || ((uintptr_t)seg_ws & 255) || seg_bytes < need)
+    return GLEMUR_ERR_WORKSPACE;
+  int nx, ny, nz, prec;
+  double h[3];
+  void *d, *B0s, *k[5], *stream;
+  int rc = ctx_info(c, &nx, &ny, &nz, h, &prec, &d, &B0s, k, &stream);
+  if (rc) return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const size_t S = (glemur_state_bytes(c) + 255) & ~(size_t)255;
+  const size_t F3 = sizeof(double) * 3 * (size_t)nx * ny * nz;
+  const long long nseg = n > 0 ? ((long long)n + every - 1) / every : 1;
+  const int per = n < every ? n : every;
+  unsigned char* base = (unsigned char*)seg_ws;
+  unsigned char* states = base + (size_t)nseg * S;  // the states after each step of a segment
+  double* scratch = (double*)(states + (size_t)per * S);
+  auto ckpt = [&](long long q) { return (void*)(base + (size_t)q * S); };
+  cudaError_t e = cudaMemsetAsync(mu_B0, 0, F3, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lam_x0, 0, F3, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, F3, s);
+  if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
+  // forward: checkpoints at steps 0, every, 2 every, ... (< n)
+  glemur_stats st;
+  if ((rc = glemur_set_x(c, x0, GLEMUR_MEM_DEVICE))) return rc;
+  if ((rc = glemur_get_state(c, ckpt(0)))) return rc;
+  for (int i = 0; i < n; ++i) {
+    if ((rc = glemur_step_fixed(c, dts[i], &st))) return rc;
+    if ((i + 1) % every == 0 && i + 1 < n && (rc = glemur_get_state(c, ckpt((i + 1) / every))))
+      return rc;
+  }
+  if (n == 0) {
+    if ((rc = glemur_set_state(c, ckpt(0)))) return rc;
+    return glemur_loss_grad(c, loss, value, lam_x0, mu_B0, adj_ws, adj_bytes);
+  }
+  // backward, segment by segment from the last
+  double* lam_next = lam_x0;
+  double* lam = scratch;
+  bool seeded = false;
+  for (long long q = nseg - 1; q >= 0; --q) {
+    const int start = (int)(q * every), end = start + every < n ? start + every : n;
+    if ((rc = glemur_set_state(c, ckpt(q)))) return rc;
+    for (int i = start; i < end; ++i) {
+      if ((rc = glemur_step_fixed(c, dts[i], &st))) return rc;
+      if ((rc = glemur_get_state(c, states + (size_t)(i - start) * S))) return rc;
+    }
+    if (!seeded) {  // the context is at the final state
+      if ((rc = glemur_loss_grad(c, loss, value, lam_next, mu_B0, adj_ws, adj_bytes))) return rc;
+      seeded = true;
+    }
+    for (int i = end - 1; i >= start; --i) {
+      const void* xi = i == start ? ckpt(q) : (const void*)(states + (size_t)(i - start - 1) * S);
+      if ((rc = glemur_set_state(c, xi))) return rc;
+      if ((rc = glemur_vjp_step(c, dts[i], lam_next, lam, mu_B0, adj_ws, adj_bytes))) return rc;
+      double* t = lam_next;
+      lam_next = lam;
+      lam = t;
+    }
+  }
+  if (lam_next != lam_x0) e = cudaMemcpyAsync(lam_x0, lam_next, F3, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GLEMUR_OK : GLEMUR_ERR_CUDA;
+}
+
 int glemur_param_contract(int n_params, long long m, const double* dB0, const double* mu,
                           double* out, void* stream) {
   if (n_params < 1 || m < 1 || !dB0 || !mu || !out) return GLEMUR_ERR_BADARG;

@@ -58,7 +58,8 @@ EXPORTS = ["glemur_default_opts", "glemur_workspace_bytes", "glemur_init_grid",
            "glemur_strerror", "glemur_adjoint_workspace_bytes", "glemur_vjp_step",
            "glemur_loss_grad", "glemur_param_contract", "glemur_state_bytes",
            "glemur_get_state", "glemur_set_state", "glemur_get_dt_schedule",
-           "glemur_deviation", "glemur_alpha_line", "glemur_convexity"]
+           "glemur_deviation", "glemur_alpha_line", "glemur_convexity",
+           "glemur_adjoint_segment_bytes", "glemur_adjoint_segment"]
 DT_LOG = 65536  # accepted step sizes the device keeps (GLEMUR_DT_LOG)
 LOSS_ENERGY, LOSS_XI = 0, 1
 
@@ -110,6 +111,10 @@ def lib() -> C.CDLL:
     L.glemur_vjp_step.argtypes = [vp, C.c_double, vp, vp, vp, vp, C.c_size_t]
     L.glemur_loss_grad.argtypes = [vp, ip, dp, vp, vp, vp, C.c_size_t]
     L.glemur_param_contract.argtypes = [ip, C.c_longlong, vp, vp, vp, vp]
+    L.glemur_adjoint_segment_bytes.argtypes = [vp, ip, ip]
+    L.glemur_adjoint_segment_bytes.restype = C.c_size_t
+    L.glemur_adjoint_segment.argtypes = [vp, vp, dp, ip, ip, ip, dp, vp, vp, vp, C.c_size_t, vp,
+                                         C.c_size_t]
     L.glemur_state_bytes.argtypes = [vp]
     L.glemur_state_bytes.restype = C.c_size_t
     L.glemur_get_state.argtypes = [vp, vp]
@@ -380,6 +385,33 @@ class Relaxation:
                                      C.c_void_p(lam.data_ptr()), C.c_void_p(mu_B0.data_ptr()),
                                      C.c_void_p(ws.data_ptr()), ws.numel()), "glemur_vjp_step")
 
+    def adjoint_segment(self, x0, dts, loss=LOSS_ENERGY, checkpoint_every=50):
+        """glemur_adjoint_segment: the loss of the state reached from the
+        positions x0 (CUDA float64 tensor) by the step sizes dts, and its
+        gradients with respect to B0 and x0 -- checkpoints every
+        `checkpoint_every` steps, recompute and the reverse steps, all in
+        the library.  Returns (value, dL/dB0, dL/dx0)."""
+        import torch
+        _field_ptr(x0, self.shape)
+        if not x0.is_cuda:
+            raise ValueError("x0 must be a CUDA tensor")
+        d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+        n, every = int(d.size), max(1, int(checkpoint_every))
+        nb = int(lib().glemur_adjoint_segment_bytes(self._h, n, every))
+        if nb == 0:
+            raise GlemurError(-1, "glemur_adjoint_segment_bytes")
+        seg = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        ws = self._adj_ws()
+        lam = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        mu = torch.empty_like(lam)
+        v = C.c_double()
+        _check(lib().glemur_adjoint_segment(
+            self._h, C.c_void_p(x0.data_ptr()), d.ctypes.data_as(C.POINTER(C.c_double)), n,
+            every, int(loss), C.byref(v), C.c_void_p(lam.data_ptr()), C.c_void_p(mu.data_ptr()),
+            C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(seg.data_ptr()), seg.numel()),
+            "glemur_adjoint_segment")
+        return v.value, mu, lam
+
     def loss_grad(self, loss, lam, mu_B0):
         """Loss of the current state; its position gradient into lam and its
         B0 gradient added to mu_B0."""
@@ -481,8 +513,7 @@ def loss_and_field_gradient(relax, x0, dts, loss=LOSS_ENERGY, checkpoint_every=5
     pass recomputes each segment forwards, storing its states, then runs the
     steps' vector-Jacobian products in reverse (glemur_vjp_step).
     """
-    ckpts = forward_checkpoints(relax, x0, dts, checkpoint_every)
-    return reverse_sweep(relax, ckpts, dts, loss, checkpoint_every)
+    return relax.adjoint_segment(x0, dts, loss, checkpoint_every)
 
 
 def _loss_value(relax, loss):

@@ -144,6 +144,39 @@ def test_parameter_gradient_through_steps(G, loss):
             (p, grad[p], d_fd)
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("n,every", [(12, 5), (7, 7), (3, 10), (0, 4)],
+                         ids=["12by5", "7by7", "3by10", "none"])
+def test_native_segment_matches_the_orchestrated_sweep(G, precision, n, every):
+    """glemur_adjoint_segment (checkpoints, recompute and reverse steps in
+    the library) against the same algorithm orchestrated call by call
+    (forward_checkpoints + reverse_sweep over glemur_get_state / set_state /
+    step_fixed / vjp_step / loss_grad): the same kernels in the same order,
+    so loss, dL/dB0 and dL/dx0 agree bit for bit, for segment lengths that
+    do and do not divide the step count, a single partial segment and no
+    steps at all."""
+    g, X, x0, regs = case(14, 13, 15)
+    B0 = gi.braid_field(X, regs)
+    dts = [2e-3 * (1.0 + 0.1 * (i % 3)) for i in range(n)]
+    r = relax_for(G, g, x0, B0, precision=precision)
+    for loss in (0, 1):
+        v1, mu1, lam1 = r.adjoint_segment(cuda(x0), dts, loss, every)
+        ck = G.forward_checkpoints(r, cuda(x0), dts, every)
+        v2, mu2, lam2 = G.reverse_sweep(r, ck, dts, loss, every)
+        assert v1 == v2
+        assert torch.equal(mu1, mu2) and torch.equal(lam1, lam2)
+        assert float(mu1.abs().max()) > 0
+
+
+def test_native_segment_argument_errors(G):
+    g, X, x0, regs = case(8, 8, 8)
+    r = relax_for(G, g, x0, gi.braid_field(X, regs))
+    with pytest.raises(G.GlemurError):
+        r.adjoint_segment(cuda(x0), [1e-3, -1.0], 0, 2)      # a step size <= 0
+    with pytest.raises(G.GlemurError):
+        r.adjoint_segment(cuda(x0), [1e-3], 5, 2)            # no such loss
+
+
 def test_autograd_function(G):
     """torch.autograd through RelaxationFieldLoss gives the field gradient."""
     g, X, x0, regs = case(10, 10, 10)
