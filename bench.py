@@ -64,6 +64,7 @@ NCU_TRAFFIC = {
     ("braid64", "mixed", "mimetic"): (15706709, "8f6eb70c2a78"),
     ("braid64", "mixed", "direct"): (15825109, "8f6eb70c2a78"),
     ("braid128", "mixed", "mimetic"): (155344939, "8f6eb70c2a78"),
+    ("prod384", "mixed", "mimetic"): (4828183893, "8f6eb70c2a78"),
 }
 
 
