@@ -309,13 +309,12 @@ bool persist_plan(glemur_ctx* c, int G) {
   const long long A = (long long)(nx - 2) * (ny - 2);
   int* h = new (std::nothrow) int[4 * (size_t)nz + 64 + (size_t)G * (2 * PERSIST_BI + 2)];
   if (!h) return false;
-  int* cnt = h;                 // cntB, cntC: zeroed per launch
+  // h[0, 2 nz): the completion counters, zeroed per launch
   int* touchB = h + 2 * nz;
   int* touchC = h + 3 * nz;
   int* ivB = h + 4 * nz + 64;
   int* ivC = ivB + (size_t)G * 2 * PERSIST_BI;
   for (int i = 0; i < 4 * nz + 64; ++i) h[i] = 0;
-  (void)cnt;
   for (int b = 0; b < G; ++b) {
     int* vb = ivB + (size_t)b * 2 * PERSIST_BI;
     for (int q = 0; q < PERSIST_BI; ++q) {
