@@ -58,3 +58,26 @@ def test_classic_is_qualitatively_table1_n17():
     assert 0.1 < eps_c < 2.0 and eps_c > 10 * eps_m
     assert 0.5 * ref["sigma_B"] < sb_c < 2.0 * ref["sigma_B"]
     assert sb_c > 5 * sb_m
+
+
+def test_mimetic_reproduces_table1_pi_over_2_n17():
+    """Table 1's phi = pi/2 row (single precision in the paper; fixture
+    tests/golden/isohelix_table1_single.json) at n = 17: epsilon*, sigma_B
+    and sigma_x are set by the discretisation, so the FP64 oracle's run
+    reproduces them (within 6 % after 600 steps)."""
+    ref = json.load(open(os.path.join(HERE, "golden", "isohelix_table1_single.json")))
+    ref = ref["mimetic"]["pi/2"]["17"]
+    w = gi.make_workload("isohelix", n=17)
+    g = w.grid
+    X = gi.nodes(g)
+    B0 = gi.isohelix_field(X, phi=math.pi / 2)
+    xr, Br = gi.isohelix_relaxed(X, phi=math.pi / 2)
+    x, _, _, st, rc = ora.relax(g, w.x0, B0, 600, 1e-2, ora.MIMETIC,
+                                opts=ora.ControlOpts(safety=0.9))
+    assert rc == ora.OK
+    _, eps, rc = ora.alpha_line(g, x, B0, 8, 8, math.sqrt(2.0), ora.MIMETIC)
+    assert rc == ora.OK
+    sx, sb, _ = ora.deviation(g, x, B0, xr, Br)
+    assert eps == pytest.approx(ref["eps_star"], rel=0.1)
+    assert sb == pytest.approx(ref["sigma_B"], rel=0.1)
+    assert sx == pytest.approx(ref["sigma_x"], rel=0.1)
