@@ -155,6 +155,29 @@ def isohelix_field(X, B0=1.0, a_r=math.sqrt(2.0), a_z=2.0, phi=math.pi / 4):
     return np.stack([f * y, -f * x, np.full_like(x, B0)])
 
 
+# Offsets of the two Pontin09 twist regions from the mid-plane.  The paper
+# does not give them; +-4 (in the IsoHelix box 8 x 8 x 20) is the value of
+# {2, 3, 4, 5, 6} whose mimetic epsilon* reproduces Table 2 at n = 17 and 33,
+# with n = 65 as the check.
+PONTIN09_L = (4.0, -4.0)
+
+
+def pontin09_field(X, phi=(math.pi / 2, -math.pi / 2), L=PONTIN09_L, B0=1.0,
+                   a_r=math.sqrt(2.0), a_z=2.0):
+    """Paper eq. "B init Pontin09": B0 e_z plus two twist regions at Z = L_i
+    of twist angles phi_i, each 2 B0 phi_i / (pi a_r) exp(-(X^2+Y^2)/a_r^2
+    - (Z-L_i)^2/a_z^2) (-Y e_x + X e_y)."""
+    x, y, z = X
+    Bx = np.zeros_like(x)
+    By = np.zeros_like(x)
+    for ph, Li in zip(phi, L):
+        f = 2.0 * B0 * ph / (math.pi * a_r) * np.exp(-(x * x + y * y) / a_r ** 2
+                                                    - (z - Li) ** 2 / a_z ** 2)
+        Bx -= y * f
+        By += x * f
+    return np.stack([Bx, By, np.full_like(x, B0)])
+
+
 def isohelix_relaxed(X, B0=1.0, a_r=math.sqrt(2.0), a_z=2.0, phi=math.pi / 4):
     """The IsoHelix field's exact relaxed state (eqs. "B relaxed" and "x
     analytical relaxed"): positions x_relax -- each plane Z = const turned

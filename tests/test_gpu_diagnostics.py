@@ -220,3 +220,35 @@ def test_isohelix_table1_stronger_twists(G):
            {kk: float(f"{vv:.3g}") for kk, vv in v.items()} for k, v in res.items()})
     assert table["pi"]["17"] is None
     assert _isohelix_twist_run(G, 17, math.pi, 0, 1) == -5     # GLEMUR_ERR_DT_UNDERFLOW
+
+
+def test_pontin09_table2(G):
+    """Table 2 (Pontin09: two twist regions of -+ pi/2, eq. "B init
+    Pontin09", single precision in the paper; fixture
+    tests/golden/pontin09_table2.json) with the mimetic current, FP64:
+    epsilon* on the central line, four times the pi/4 run length (settled:
+    the same at eight times), within 10 % of the printed value at n = 17
+    and 33 (measured 4 % and 2 %) and within 15 % at n = 65 (measured 12 %
+    above).  The paper does not give the regions' offsets from the
+    mid-plane; the reading +-4 was chosen from {2, 3, 4, 5, 6} by the
+    n = 17 and 33 rows, so n = 65 is the check."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                      "pontin09_table2.json")))["mimetic"]
+    out = {}
+    for n, mult, tol in ((17, 4, 0.1), (33, 4, 0.1), (65, 4, 0.15)):
+        w = gi.make_workload("isohelix", n=n)
+        g = w.grid
+        B0 = gi.pontin09_field(gi.nodes(g))
+        r = relaxation(G, g, w.x0, B0, dt0=1e-2, safety=0.9)
+        st = r.step(mult * 1200 * (n - 1) ** 2 // 256)
+        assert st["status"] == 0
+        c = (n - 1) // 2
+        _, eps = r.alpha_line(c, c, math.sqrt(2.0))
+        xi, _ = r.forcefree_err()
+        out[n] = (eps, xi)
+        assert eps == pytest.approx(ref[str(n)]["eps_star"], rel=tol), (n, eps)
+        assert xi < 1e-3
+    print({n: (float(f"{e:.3g}"), float(f"{x:.3g}")) for n, (e, x) in out.items()})
+    assert out[65][0] < out[33][0] < out[17][0]
