@@ -223,7 +223,7 @@ def test_isohelix_table1_stronger_twists(G):
 
 
 def test_pontin09_table2(G):
-    """Table 2 (Pontin09: two twist regions of -+ pi/2, eq. "B init
+    """Table 2 (Pontin09: two twist regions of +-pi/2, eq. "B init
     Pontin09", single precision in the paper; fixture
     tests/golden/pontin09_table2.json) with the mimetic current, FP64:
     epsilon* on the central line, four times the pi/4 run length (settled:
