@@ -252,3 +252,34 @@ def test_pontin09_table2(G):
         assert xi < 1e-3
     print({n: (float(f"{e:.3g}"), float(f"{x:.3g}")) for n, (e, x) in out.items()})
     assert out[65][0] < out[33][0] < out[17][0]
+
+
+def test_pontin09_pi_mimetic_better_but_less_stable(G):
+    """The paper's finding for the Pontin09 field at twists +-pi (its
+    figure of epsilon* over time): the mimetic current reaches a far more
+    force-free state but lacks stability for this field.  Here, over the pi/4
+    run length: at n = 17 the mimetic run's step size collapses
+    (DT_UNDERFLOW) while the classic run completes with a convex grid; at
+    n = 65 both complete, the mimetic epsilon* 8 times below the classic one
+    (0.040 against 0.33) on a grid that has lost convexity at thousands of
+    nodes, the classic grid at none."""
+    def run(n, curl):
+        w = gi.make_workload("isohelix", n=n)
+        g = w.grid
+        B0 = gi.pontin09_field(gi.nodes(g), phi=(math.pi, -math.pi))
+        r = relaxation(G, g, w.x0, B0, curl=curl, dt0=1e-2, safety=0.9)
+        try:
+            r.step(1200 * (n - 1) ** 2 // 256)
+        except G.GlemurError as e:
+            return e.code
+        c = (n - 1) // 2
+        _, eps = r.alpha_line(c, c, math.sqrt(2.0))
+        return {"eps_star": eps, "concave": r.convexity()}
+
+    assert run(17, G.MIMETIC) == -5                  # GLEMUR_ERR_DT_UNDERFLOW
+    c17 = run(17, G.DIRECT)
+    assert isinstance(c17, dict) and c17["concave"] == 0
+    m65, c65 = run(65, G.MIMETIC), run(65, G.DIRECT)
+    assert isinstance(m65, dict) and isinstance(c65, dict), (m65, c65)
+    assert m65["eps_star"] < c65["eps_star"] / 5
+    assert m65["concave"] > 0 and c65["concave"] == 0
