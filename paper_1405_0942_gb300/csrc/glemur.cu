@@ -205,7 +205,6 @@ struct glemur_ctx {
   TmaMaps maps;                          // their tensor maps
   void* ys[2];                           // mimetic stages: stage inputs y_1..y_5
   double* Bb;                            // split path: B
-  double* rb;                            // split path: 1/det G
   double* Gb;                            // split path: g_0, g_1, g_2
   int max_blocks, nblocks, kz;          // mimetic-current launches
   int split_grid_b[6] = {}, split_grid_c[6] = {};  // FP64 two-pass grids (CTAs)
@@ -254,10 +253,9 @@ Layout layout(int nx, int ny, int nz, int precision) {
                   ? align256(sizeof(int) * (4 * (size_t)nz + 64 +
                                             (size_t)PERSIST_MAX_CTAS * (2 * PERSIST_BI + 2)))
                   : 0;
-  // two stage inputs (mimetic stages); FP64 also B and 1/det G for the
-  // two-pass stages
+  // two stage inputs (mimetic stages); FP64 also B and the node records
+  // (differences and 1/det G) of the two-pass stages
   L.split = 2 * L.field + (precision == GLEMUR_FP64 ? align256((size_t)(3 * N) * 8) +
-                                                          align256((size_t)N * 8) +
                                                           align256((size_t)(10 * N) * 8)
                                                     : 0);
   L.total = 8 * L.field + L.stage + L.part + L.state + L.ptrs + L.dtlog + L.persist + L.split;
@@ -892,12 +890,11 @@ int glemur_init_grid(glemur_ctx** out, int nx, int ny, int nz, const double lo[3
   c->persist_base = (int*)p; p += L.persist;
   c->max_blocks = L.max_blocks;
   c->split = 0;
-  c->ys[0] = c->ys[1] = c->Bb = c->rb = c->Gb = nullptr;
+  c->ys[0] = c->ys[1] = c->Bb = c->Gb = nullptr;
   c->ys[0] = p; p += L.field;
   c->ys[1] = p; p += L.field;
   if (o.precision == GLEMUR_FP64) {
     c->Bb = (double*)p; p += align256((size_t)(3 * c->N) * 8);
-    c->rb = (double*)p; p += align256((size_t)c->N * 8);
     c->Gb = (double*)p;
     const char* fused = getenv("GLEMUR_F64_FUSED");
     // the next-nearest-neighbour current exists in the two-pass form only
