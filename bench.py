@@ -57,14 +57,14 @@ MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # captured from (kernel_source_hash()); a workload without an entry, or one
 # whose kernels have changed since, reports null
 NCU_TRAFFIC = {
-    ("braid64", "fp64", "mimetic"): (58569301, "0ed7f14c08a5"),
-    ("braid64", "fp64", "direct"): (31328640, "0ed7f14c08a5"),
-    ("braid64", "fp64", "nnn"): (44228480, "0ed7f14c08a5"),
-    ("periodic64", "fp64", "mimetic"): (58363819, "0ed7f14c08a5"),
-    ("braid64", "mixed", "mimetic"): (15707179, "0ed7f14c08a5"),
-    ("braid64", "mixed", "direct"): (15827883, "0ed7f14c08a5"),
-    ("braid128", "mixed", "mimetic"): (152628309, "0ed7f14c08a5"),
-    ("prod384", "mixed", "mimetic"): (4828624811, "0ed7f14c08a5"),
+    ("braid64", "fp64", "mimetic"): (58571264, "c66df4c875fa"),
+    ("braid64", "fp64", "direct"): (31334571, "c66df4c875fa"),
+    ("braid64", "fp64", "nnn"): (44228053, "c66df4c875fa"),
+    ("periodic64", "fp64", "mimetic"): (58348800, "c66df4c875fa"),
+    ("braid64", "mixed", "mimetic"): (15707093, "c66df4c875fa"),
+    ("braid64", "mixed", "direct"): (15829205, "c66df4c875fa"),
+    ("braid128", "mixed", "mimetic"): (152640683, "c66df4c875fa"),
+    ("prod384", "mixed", "mimetic"): (4828091392, "c66df4c875fa"),
 }
 
 
