@@ -320,8 +320,12 @@ __device__ __forceinline__ void pass_B(const SplitArgs& a, int cur, double* red)
   }
 }
 
+// No minimum-CTA bound: the later stages' pass B fits 64 registers (four
+// CTAs per SM) by itself, the first (with the energy sum) takes 76 (three
+// CTAs, its grid sized to match); forcing four CTAs on every stage made each
+// of them spill.
 template <int S>
-__global__ void __launch_bounds__(256, 4) k_split_B(const SplitArgs a) {
+__global__ void __launch_bounds__(256) k_split_B(const SplitArgs a) {
   pdl_wait();
   const DevState* st = a.st;
   if (!a.force && (st->status != ST_OK || st->n_accept >= st->target)) return;
