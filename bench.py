@@ -57,14 +57,14 @@ MIN_TIMED_S = 1.0              # repeat the block of timed attempts until this
 # captured from (kernel_source_hash()); a workload without an entry, or one
 # whose kernels have changed since, reports null
 NCU_TRAFFIC = {
-    ("braid64", "fp64", "mimetic"): (58571264, "c66df4c875fa"),
-    ("braid64", "fp64", "direct"): (31334571, "c66df4c875fa"),
-    ("braid64", "fp64", "nnn"): (44228053, "c66df4c875fa"),
-    ("periodic64", "fp64", "mimetic"): (58348800, "c66df4c875fa"),
-    ("braid64", "mixed", "mimetic"): (15707093, "c66df4c875fa"),
-    ("braid64", "mixed", "direct"): (15829205, "c66df4c875fa"),
-    ("braid128", "mixed", "mimetic"): (152640683, "c66df4c875fa"),
-    ("prod384", "mixed", "mimetic"): (4828091392, "c66df4c875fa"),
+    ("braid64", "fp64", "mimetic"): (58517077, "12ef320afb68"),
+    ("braid64", "fp64", "direct"): (31328939, "12ef320afb68"),
+    ("braid64", "fp64", "nnn"): (44177536, "12ef320afb68"),
+    ("periodic64", "fp64", "mimetic"): (58309376, "12ef320afb68"),
+    ("braid64", "mixed", "mimetic"): (15706752, "12ef320afb68"),
+    ("braid64", "mixed", "direct"): (15828949, "12ef320afb68"),
+    ("braid128", "mixed", "mimetic"): (152739371, "12ef320afb68"),
+    ("prod384", "mixed", "mimetic"): (4827807787, "12ef320afb68"),
 }
 
 
