@@ -81,3 +81,20 @@ def test_mimetic_reproduces_table1_pi_over_2_n17():
     assert eps == pytest.approx(ref["eps_star"], rel=0.1)
     assert sb == pytest.approx(ref["sigma_B"], rel=0.1)
     assert sx == pytest.approx(ref["sigma_x"], rel=0.1)
+
+
+def test_pontin09_reproduces_table2_n17():
+    """Table 2's mimetic row at n = 17 (Pontin09, twists +-pi/2; fixture
+    tests/golden/pontin09_table2.json), the oracle with the offset reading
+    +-4 (glemur_inputs.PONTIN09_L): epsilon* within 10 % after 600 steps
+    (0.118 against 0.11)."""
+    ref = json.load(open(os.path.join(HERE, "golden", "pontin09_table2.json")))
+    w = gi.make_workload("isohelix", n=17)
+    g = w.grid
+    B0 = gi.pontin09_field(gi.nodes(g))
+    x, _, _, st, rc = ora.relax(g, w.x0, B0, 600, 1e-2, ora.MIMETIC,
+                                opts=ora.ControlOpts(safety=0.9))
+    assert rc == ora.OK
+    _, eps, rc = ora.alpha_line(g, x, B0, 8, 8, math.sqrt(2.0), ora.MIMETIC)
+    assert rc == ora.OK
+    assert eps == pytest.approx(ref["mimetic"]["17"]["eps_star"], rel=0.1)
