@@ -70,3 +70,18 @@ def test_nnn_roofline_uses_its_own_flop_count():
     I = 62 ** 3
     assert np.isclose(r["achieved"], 729.0 * I * 6 / 1e-3 / 1e12)
     assert r["algorithmic_flops_per_launch"] == 729.0 * I
+
+
+def test_traffic_table_covers_the_default_run_on_the_current_kernels():
+    """Every stage-kernel roofline the default benchmark line carries (the
+    headline and its comparison modes) has a traffic figure captured on the
+    current stage-kernel sources, so none of them reports null."""
+    h = bench.kernel_source_hash()
+    modes = [("braid64", "fp64", "mimetic"), ("braid64", "mixed", "mimetic"),
+             ("braid64", "fp64", "direct"), ("braid64", "mixed", "direct"),
+             ("braid64", "fp64", "nnn"), ("periodic64", "fp64", "mimetic"),
+             ("braid128", "mixed", "mimetic"), ("prod384", "mixed", "mimetic")]
+    for m in modes:
+        assert m in bench.NCU_TRAFFIC, m
+        assert bench.NCU_TRAFFIC[m][1] == h, (m, bench.NCU_TRAFFIC[m][1], h)
+        assert bench.ncu_traffic(*m) > 0
