@@ -365,7 +365,8 @@ size_t glemur_adjoint_segment_bytes(glemur_ctx* ctx, int n_steps, int every);
  * backward: each segment recomputed forwards from its checkpoint with its
  * states kept, the loss gradient seeded at the final state, and the steps'
  * glemur_vjp_step in reverse -- checkpointing with recompute, memory
- * O(n_steps/every + every) states.  x0 must not alias the workspaces;
+ * O(n_steps/every + every) states.  x0 must not alias the workspaces (it
+ * may be lam_x0 or mu_B0: it is read before they are written);
  * seg_ws (256-byte aligned, glemur_adjoint_segment_bytes) and adj_ws (as
  * for glemur_vjp_step) are caller-owned.  Leaves the context at state x0
  * and synchronises its stream.  Errors: BADARG, WORKSPACE, CUDA and those

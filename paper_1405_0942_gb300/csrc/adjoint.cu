@@ -952,14 +952,15 @@ int glemur_adjoint_segment(glemur_ctx* c, const double* x0, const double* dts, i
   unsigned char* states = base + (size_t)nseg * S;  // the states after each step of a segment
   double* scratch = (double*)(states + (size_t)per * S);
   auto ckpt = [&](long long q) { return (void*)(base + (size_t)q * S); };
+  // forward: checkpoints at steps 0, every, 2 every, ... (< n); x0 is read
+  // before the outputs are cleared, so it may share a buffer with them
+  glemur_stats st;
+  if ((rc = glemur_set_x(c, x0, GLEMUR_MEM_DEVICE))) return rc;
+  if ((rc = glemur_get_state(c, ckpt(0)))) return rc;
   cudaError_t e = cudaMemsetAsync(mu_B0, 0, F3, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(lam_x0, 0, F3, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, F3, s);
   if (e != cudaSuccess) return GLEMUR_ERR_CUDA;
-  // forward: checkpoints at steps 0, every, 2 every, ... (< n)
-  glemur_stats st;
-  if ((rc = glemur_set_x(c, x0, GLEMUR_MEM_DEVICE))) return rc;
-  if ((rc = glemur_get_state(c, ckpt(0)))) return rc;
   for (int i = 0; i < n; ++i) {
     if ((rc = glemur_step_fixed(c, dts[i], &st))) return rc;
     if ((i + 1) % every == 0 && i + 1 < n && (rc = glemur_get_state(c, ckpt((i + 1) / every))))
