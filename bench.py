@@ -23,7 +23,6 @@ import argparse
 import glob
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
